@@ -1,0 +1,169 @@
+/*
+ * hotrg.h -- C ABI of libhotrg, a GB300 (sm_103a) implementation of the HOTRG
+ * coarse-graining step for 2D classical lattice models.
+ *
+ * The method: the partition function of a 2D spin model is the contraction of
+ * N copies of a local tensor, Z = Tr T^N (Sec. II.A, Eq. 2).  One HOTRG step
+ * contracts two neighbouring tensors along one bond, fuses the two parallel
+ * legs that result and cuts each fused leg back to at most D_cut states by a
+ * higher-order SVD that reduces to the SVD of a reshaped matrix (Sec. II.A),
+ * here the eigendecomposition of the Hermitian Gram matrix of that reshaped
+ * matrix (the Hermitian case of Eq. 5).  Contraction and SVD are the two
+ * steps that carry the cost (Sec. II.A, last paragraph).
+ *
+ * Conventions used throughout:
+ *   - A tensor T[x, x', y, y'] has legs (left, right, down, up) and shape
+ *     (Dx, Dx, Dy, Dy), stored row-major in FP64 (y' fastest).
+ *   - A Y step contracts the up leg of a lower tensor with the down leg of an
+ *     upper tensor and cuts the fused x legs; an X step does the same along x
+ *     and cuts the fused y legs.  The same isometry U projects both fused legs.
+ *   - U is taken from the left or the right environment (Gram matrix of the
+ *     two unfoldings of the contracted pair), whichever discards the smaller
+ *     eigenvalue weight; ties go to the left.  If Dx^2 <= D_cut nothing is cut.
+ *   - After every step the tensor is divided by its max-norm c_n and
+ *     ln(c_n) / 2^n is added to an FP64 log-sum; the initial tensor is scaled
+ *     by c_0 = max|T0| the same way.  After n steps the network holds 2^n
+ *     sites and ln Z / N = logsum + ln(Tr T_n) / 2^n, Tr the periodic trace.
+ *
+ * Ownership and errors:
+ *   - Every host buffer stays owned by the caller; the library copies what it
+ *     needs before returning.  A context owns all device memory it uses and
+ *     releases it in hotrg_destroy.
+ *   - No C++ exception crosses this interface.  Every call returns a status;
+ *     the first error seen by a context is latched: later calls on it return
+ *     the same status without doing work, and hotrg_last_error() returns a
+ *     message.  A NULL context pointer gives HOTRG_EINVAL.
+ *   - hotrg_step enqueues work on the context's stream.  It synchronises that
+ *     stream once per step (the eigensolver reports its result count to the
+ *     host); device-side faults surface at the next synchronising call.
+ *   - A context may be used by one host thread at a time.
+ */
+#ifndef HOTRG_H
+#define HOTRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hotrg_ctx hotrg_ctx;
+
+typedef enum {
+  HOTRG_OK = 0,
+  HOTRG_EINVAL = 1,      /* bad argument (NULL pointer, size, enum value)            */
+  HOTRG_ENOMEM = 2,      /* device or host allocation failed                         */
+  HOTRG_ECUDA = 3,       /* CUDA runtime or library error                            */
+  HOTRG_EEIG = 4,        /* the eigensolver did not converge or rejected its input    */
+  HOTRG_ENONFINITE = 5,  /* max-norm or trace is zero, negative or not finite         */
+  HOTRG_ETIMEOUT = 6,    /* a bounded device wait ran out                            */
+  HOTRG_ESTATE = 7       /* call not valid in the context's current state            */
+} hotrg_status;
+
+typedef enum { HOTRG_DIR_X = 0, HOTRG_DIR_Y = 1 } hotrg_dir;
+
+/*
+ * Arithmetic of the contraction GEMMs (environment partials, Gram combine,
+ * projection chain).  The environment eigendecomposition, the max-norm, the
+ * log-sum and the trace are FP64 in every mode.
+ *   HOTRG_FP64    FP64 SIMT GEMMs (the plain reference path on the GPU).
+ *   HOTRG_TF32    tcgen05 kind::tf32 tensor-core GEMMs, FP32 accumulation.
+ *   HOTRG_BF16X3  tcgen05 kind::f16 with each operand split into two BF16
+ *                 terms a = a_hi + a_lo; products hi*hi + hi*lo + lo*hi,
+ *                 FP32 accumulation.
+ *   HOTRG_BF16X6  three-term BF16 split a = a1 + a2 + a3; the six products
+ *                 whose term indices sum to at most 4, FP32 accumulation.
+ */
+typedef enum { HOTRG_FP64 = 0, HOTRG_TF32 = 1, HOTRG_BF16X3 = 2, HOTRG_BF16X6 = 3 } hotrg_prec;
+
+/* Per-step diagnostics (all gauge-invariant except ln_c, see hotrg_step_info). */
+typedef struct {
+  int dir;          /* HOTRG_DIR_X or HOTRG_DIR_Y                                  */
+  int Dx;           /* dimension of the fused legs before the step (step's view)   */
+  int Dy;           /* dimension of the contracted legs                            */
+  int Dn;           /* kept dimension D' = min(Dx^2, D_cut)                         */
+  int side;         /* 0 = left env chosen, 1 = right, -1 = nothing cut (U = I)    */
+  double ln_c;      /* ln max|T'| before the rescale                               */
+  double eps_L;     /* Tr G_L - sum of its D' leading eigenvalues (discarded weight) */
+  double eps_R;     /* same for G_R                                               */
+  double cut_gap;   /* (lambda_D' - lambda_{D'+1}) / lambda_1 of the chosen side, or
+                       +inf when nothing is cut                                     */
+  double trace_G;   /* Tr G_L (= ||M||_F^2)                                        */
+} hotrg_step_info_t;
+
+/*
+ * Initial tensors (Sec. II.A, Eq. 2: the local tensor whose N-fold contraction
+ * is Z).  T0[x,x',y,y'] = sum_s w_s W[s,x] W[s,x'] W[s,y] W[s,y'] with W the
+ * symmetric square root of the bond Boltzmann matrix B and w_s the site weight.
+ *   Ising (J = 1, s = +1, -1 at index 0, 1): B[s,s'] = exp(beta s s'),
+ *     w_s = exp(beta h s); T0_out receives 16 doubles.  Needs beta > 0.
+ *   Potts (q states, J = 1, no field): B[s,s'] = exp(beta delta_{ss'}), w = 1;
+ *     T0_out receives q^4 doubles.  Needs beta > 0 and 2 <= q <= 16.
+ * Host-only; no device is touched.  Returns HOTRG_EINVAL on bad arguments.
+ */
+hotrg_status hotrg_ising_tensor(double beta, double h, double *T0_out);
+hotrg_status hotrg_potts_tensor(int q, double beta, double *T0_out);
+
+/*
+ * Create a context holding T0 (host, D0^4 doubles, [x,x',y,y'] row-major,
+ * borrowed and copied) scaled by its max-norm, ready for steps with cut D_cut.
+ * stream: a cudaStream_t (NULL = the legacy default stream); the context
+ * enqueues all its work there.  All device memory for steps up to D_cut is
+ * allocated here (HOTRG_ENOMEM if it does not fit).  On failure *out is set to
+ * NULL.  Requires 1 <= D0 <= 64, 1 <= D_cut <= 64.
+ */
+hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec,
+                          void *stream, hotrg_ctx **out);
+
+/*
+ * One coarse-graining step in direction dir (Sec. II.A): environments, FP64
+ * eigendecomposition and choice of U, projection T' = U^T (T.T) U, max-norm
+ * rescale and log-sum update.  See the header comment for the synchronisation.
+ */
+hotrg_status hotrg_step(hotrg_ctx *ctx, hotrg_dir dir);
+
+/* ln Z / N after the steps taken so far (synchronises; one small D2H read). */
+hotrg_status hotrg_log_z_per_site(hotrg_ctx *ctx, double *out);
+
+/* f = -(1/beta) ln Z / N (synchronises).  beta must be > 0. */
+hotrg_status hotrg_free_energy(hotrg_ctx *ctx, double beta, double *f_out);
+
+/* Diagnostics of step `step` (0-based, < number of steps taken). */
+hotrg_status hotrg_step_info(hotrg_ctx *ctx, int step, hotrg_step_info_t *out);
+
+/*
+ * Normalised spectrum lambda_i / lambda_1 (descending) of the chosen
+ * environment of step `step`: the D' kept values, plus lambda_{D'+1} when a
+ * cut was made.  Writes min(cap, count) values to buf and the count to *n.
+ */
+hotrg_status hotrg_spectrum(hotrg_ctx *ctx, int step, double *buf, int cap, int *n);
+
+/*
+ * Copy the current normalised tensor to host memory (FP64, [x,x',y,y']
+ * row-major).  dims[4] receives (Dx, Dx, Dy, Dy); cap is the capacity of
+ * host_out in doubles (HOTRG_EINVAL if too small; dims are still written).
+ */
+hotrg_status hotrg_get_tensor(hotrg_ctx *ctx, double *host_out, long long cap, int dims[4]);
+
+/*
+ * Copy the isometry U of the last step to host memory, column-major
+ * (rows = Dx^2 fused index (x1 x2) with x1 slower, cols = D'), and its shape.
+ */
+hotrg_status hotrg_get_isometry(hotrg_ctx *ctx, double *host_out, long long cap,
+                                int *rows, int *cols);
+
+/* Current bond dimensions (Dx, Dy) and number of steps taken. */
+hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
+
+/* Release all resources of the context; NULL is accepted and ignored. */
+void hotrg_destroy(hotrg_ctx *ctx);
+
+/* Message of the latched error ("" if none); valid until the next call on ctx. */
+const char *hotrg_last_error(const hotrg_ctx *ctx);
+
+/* Static name of a status code. */
+const char *hotrg_status_string(hotrg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOTRG_H */

@@ -1,0 +1,199 @@
+"""ctypes binding of libhotrg's C ABI (``include/hotrg.h``).
+
+Argument marshalling only: every step of the coarse-graining runs in the
+library's CUDA kernels.  The shared object is built in-tree by
+``paper_2602_05900_gb300.build`` (``__graft_entry__.build()``); if it is
+missing, loading fails loudly -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhotrg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hotrg.h")
+
+HOTRG_OK, HOTRG_EINVAL, HOTRG_ENOMEM, HOTRG_ECUDA, HOTRG_EEIG, HOTRG_ENONFINITE, \
+    HOTRG_ETIMEOUT, HOTRG_ESTATE = range(8)
+DIR_X, DIR_Y = 0, 1
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3}
+
+
+class StepInfo(ctypes.Structure):
+    """Mirror of ``hotrg_step_info_t``."""
+    _fields_ = [("dir", ctypes.c_int), ("Dx", ctypes.c_int), ("Dy", ctypes.c_int),
+                ("Dn", ctypes.c_int), ("side", ctypes.c_int), ("ln_c", ctypes.c_double),
+                ("eps_L", ctypes.c_double), ("eps_R", ctypes.c_double),
+                ("cut_gap", ctypes.c_double), ("trace_G", ctypes.c_double)]
+
+
+class HotrgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_SIGS = {
+    "hotrg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hotrg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hotrg_ising_tensor": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _dp]),
+    "hotrg_potts_tensor": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _dp]),
+    "hotrg_create": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "hotrg_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hotrg_log_z_per_site": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "hotrg_free_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dp]),
+    "hotrg_step_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StepInfo)]),
+    "hotrg_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int, _ip]),
+    "hotrg_get_tensor": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_longlong, _ip]),
+    "hotrg_get_isometry": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_longlong, _ip, _ip]),
+    "hotrg_dims": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip]),
+    "hotrg_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the functions declared in ``include/hotrg.h``."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hotrg_[a-z_0-9]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libhotrg.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"libhotrg.so not found at {path}; run __graft_entry__.build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return load().hotrg_status_string(s).decode()
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def ising_tensor(beta: float, h: float = 0.0) -> np.ndarray:
+    out = np.zeros((2, 2, 2, 2))
+    s = load().hotrg_ising_tensor(beta, h, _ptr(out))
+    if s:
+        raise HotrgError(s, "hotrg_ising_tensor rejected its arguments")
+    return out
+
+
+def potts_tensor(q: int, beta: float) -> np.ndarray:
+    out = np.zeros((q, q, q, q))
+    s = load().hotrg_potts_tensor(q, beta, _ptr(out))
+    if s:
+        raise HotrgError(s, "hotrg_potts_tensor rejected its arguments")
+    return out
+
+
+class Hotrg:
+    """One HOTRG instance on the GPU (owns a ``hotrg_ctx``)."""
+
+    def __init__(self, T0: np.ndarray, D_cut: int, precision: str = "fp64", stream=None):
+        lib = load()
+        T0 = np.ascontiguousarray(T0, dtype=np.float64)
+        D0 = T0.shape[0]
+        if T0.shape != (D0, D0, D0, D0):
+            raise ValueError("T0 must have shape (D0, D0, D0, D0)")
+        handle = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else
+                             (stream.cuda_stream if stream is not None else 0))
+        s = lib.hotrg_create(_ptr(T0), D0, int(D_cut), PRECISIONS[precision], st,
+                             ctypes.byref(handle))
+        if s:
+            raise HotrgError(s, f"hotrg_create failed: {status_string(s)}")
+        self._h = handle
+        self.D_cut = int(D_cut)
+        self.precision = precision
+
+    def _check(self, s: int, what: str):
+        if s:
+            msg = load().hotrg_last_error(self._h)
+            raise HotrgError(s, f"{what}: {status_string(s)}: {msg.decode() if msg else ''}")
+
+    def step(self, direction: str):
+        self._check(load().hotrg_step(self._h, DIR_X if direction == "x" else DIR_Y), "hotrg_step")
+
+    def run(self, nsteps: int, first: str = "x"):
+        for i in range(nsteps):
+            self.step(first if i % 2 == 0 else ("y" if first == "x" else "x"))
+        return self
+
+    def ln_z_per_site(self) -> float:
+        out = ctypes.c_double()
+        self._check(load().hotrg_log_z_per_site(self._h, ctypes.byref(out)), "hotrg_log_z_per_site")
+        return out.value
+
+    def free_energy(self, beta: float) -> float:
+        out = ctypes.c_double()
+        self._check(load().hotrg_free_energy(self._h, beta, ctypes.byref(out)), "hotrg_free_energy")
+        return out.value
+
+    def step_info(self, step: int) -> StepInfo:
+        out = StepInfo()
+        self._check(load().hotrg_step_info(self._h, step, ctypes.byref(out)), "hotrg_step_info")
+        return out
+
+    def spectrum(self, step: int) -> np.ndarray:
+        n = ctypes.c_int()
+        buf = np.zeros(self.D_cut + 2)
+        self._check(load().hotrg_spectrum(self._h, step, _ptr(buf), buf.size, ctypes.byref(n)),
+                    "hotrg_spectrum")
+        return buf[: n.value].copy()
+
+    def dims(self):
+        dx, dy, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(load().hotrg_dims(self._h, ctypes.byref(dx), ctypes.byref(dy), ctypes.byref(ns)),
+                    "hotrg_dims")
+        return dx.value, dy.value, ns.value
+
+    def tensor(self) -> np.ndarray:
+        dx, dy, _ = self.dims()
+        out = np.zeros((dx, dx, dy, dy))
+        dims = (ctypes.c_int * 4)()
+        self._check(load().hotrg_get_tensor(self._h, _ptr(out), out.size, dims), "hotrg_get_tensor")
+        return out
+
+    def isometry(self) -> np.ndarray:
+        rows, cols = ctypes.c_int(), ctypes.c_int()
+        load().hotrg_get_isometry(self._h, None, 0, ctypes.byref(rows), ctypes.byref(cols))
+        out = np.zeros(rows.value * cols.value)
+        self._check(load().hotrg_get_isometry(self._h, _ptr(out), out.size, ctypes.byref(rows),
+                                              ctypes.byref(cols)), "hotrg_get_isometry")
+        return out.reshape(cols.value, rows.value).T.copy()   # column-major -> [row, col]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().hotrg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,414 @@
+// tcgen05 tensor-core GEMM with TMA operand staging (sm_103a).
+//
+// One CTA computes a 128 x BN tile of C = sum_products A_p . B_q^T:
+//   warp 0 / lane 0   TMA producer: 128-byte-swizzled K-major tiles of every
+//                     operand plane into a STAGES-deep shared-memory ring;
+//   warp 1 / lane 0   MMA issuer: tcgen05.mma (kind::tf32 or kind::f16) into a
+//                     128 x BN FP32 accumulator in tensor memory, one commit per
+//                     stage to release it back to the producer;
+//   warps 0-3         epilogue: tcgen05.ld of the thread's accumulator row,
+//                     stores through the output index maps.
+// Every mbarrier wait is bounded (about a second); on timeout the kernel sets
+// *err_flag, waits (bounded) for its own TMA copies in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tc_gemm.cuh"
+
+namespace hotrg {
+namespace {
+
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at the GB300 boost clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle: rows of 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused with swizzle)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset between 8-row groups
+  d |= static_cast<uint64_t>(1) << 46;            // descriptor version of the sm_100 family
+  d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t make_idesc(bool tf32, int M, int N) {
+  return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float round_tf32(float v) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void store_out(const TcEpilogue &e, long long off, float v) {
+  switch (e.kind) {
+    case OutKind::F32:
+      static_cast<float *>(e.C)[off] = e.round_tf32 ? round_tf32(v) : v;
+      break;
+    case OutKind::F64:
+      static_cast<double *>(e.C)[off] = static_cast<double>(v);
+      break;
+    case OutKind::BF16P: {
+      __nv_bfloat16 *c = static_cast<__nv_bfloat16 *>(e.C);
+      float r = v;
+      for (int p = 0; p < e.planes; ++p) {
+        __nv_bfloat16 t = __float2bfloat16_rn(r);
+        c[off + p * e.plane_stride] = t;
+        r -= __bfloat162float(t);
+      }
+      break;
+    }
+  }
+}
+
+template <int MODE>
+struct ModeTraits;
+template <>
+struct ModeTraits<0> {  // TF32
+  static constexpr bool kTf32 = true;
+  static constexpr int kPlanes = 1, kBK = 32, kMmaK = 8, kProducts = 1;
+  __device__ static void product(int, int &pa, int &pb) { pa = 0; pb = 0; }
+};
+template <>
+struct ModeTraits<1> {  // BF16 x3: hi.hi, hi.lo, lo.hi (small terms issued first)
+  static constexpr bool kTf32 = false;
+  static constexpr int kPlanes = 2, kBK = 64, kMmaK = 16, kProducts = 3;
+  __device__ static void product(int i, int &pa, int &pb) {
+    const int a[3] = {0, 1, 0}, b[3] = {1, 0, 0};
+    pa = a[i];
+    pb = b[i];
+  }
+};
+template <>
+struct ModeTraits<2> {  // BF16 x6: every (p, q) with p + q <= 2, smallest first
+  static constexpr bool kTf32 = false;
+  static constexpr int kPlanes = 3, kBK = 64, kMmaK = 16, kProducts = 6;
+  __device__ static void product(int i, int &pa, int &pb) {
+    const int a[6] = {0, 1, 2, 0, 1, 0}, b[6] = {2, 1, 0, 1, 0, 0};
+    pa = a[i];
+    pb = b[i];
+  }
+};
+
+template <int MODE, int BN>
+struct Cfg {
+  using Tr = ModeTraits<MODE>;
+  static constexpr int BM = 128;
+  static constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = Tr::kPlanes * (A_BYTES + B_BYTES);
+  static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static_assert(STAGES >= 2, "pipeline needs two stages");
+};
+
+template <int MODE, int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+              int M, int N, int K, TcEpilogue epi, int *err_flag) {
+  using C = Cfg<MODE, BN>;
+  using Tr = typename C::Tr;
+  constexpr int STAGES = C::STAGES;
+  constexpr uint32_t IDESC = make_idesc(Tr::kTf32, C::BM, BN);
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_fail, s_issued, s_consumed;
+
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * C::BM, n0 = blockIdx.y * BN;
+  const int nkb = (K + Tr::kBK - 1) / Tr::kBK;
+
+  auto a_tile = [&](int s, int p) { return smem_base + s * C::STAGE_BYTES + p * C::A_BYTES; };
+  auto b_tile = [&](int s, int p) {
+    return smem_base + s * C::STAGE_BYTES + Tr::kPlanes * C::A_BYTES + p * C::B_BYTES;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+    int kb = 0;
+    for (; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, C::STAGE_BYTES);
+      for (int p = 0; p < Tr::kPlanes; ++p) tma_load_3d(a_tile(s, p), &ta, fb, kb * Tr::kBK, m0, p);
+      for (int p = 0; p < Tr::kPlanes; ++p) tma_load_3d(b_tile(s, p), &tb, fb, kb * Tr::kBK, n0, p);
+    }
+    s_issued = kb;
+  } else if (warp == 1 && lane == 0) {
+    int kb = 0;
+    for (; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < Tr::kBK / Tr::kMmaK; ++k) {
+#pragma unroll
+        for (int q = 0; q < Tr::kProducts; ++q) {
+          int pa, pb;
+          Tr::product(q, pa, pb);
+          const uint64_t ad = sw128_desc(a_tile(s, pa) + k * 32);
+          const uint64_t bd = sw128_desc(b_tile(s, pb) + k * 32);
+          mma_issue<Tr::kTf32>(tmem, ad, bd, IDESC, (kb | k | q) != 0);
+        }
+      }
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    s_consumed = kb;
+    mma_commit(smem_u32(&acc_bar));
+  }
+  __syncwarp();
+
+  // ---- epilogue: thread (warp w, lane l) owns accumulator row 32 w + l
+  const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0);
+  tc_fence_after();
+  if (!acc_ok) atomicExch(&s_fail, 1);
+  const bool ok = acc_ok && (*(volatile int *)&s_fail == 0);
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const bool rv = row < M;
+    const long long roff = rv ? map_off(epi.cm, row) : 0;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      if (n0 + c * 32 >= N) break;
+      uint32_t r[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, r);
+      const int col = n0 + c * 32 + lane;
+      const long long coff = (col < N) ? map_off(epi.cn, col) : -1;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const long long co = __shfl_sync(0xffffffffu, coff, j);
+        if (rv && co >= 0) store_out(epi, roff + co, __uint_as_float(r[j]));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_fail) atomicExch(err_flag, 2);
+    // TMA copies issued but never consumed (only after a timeout): let them land
+    for (int kb = s_consumed; kb < s_issued; ++kb)
+      (void)mbar_wait(smem_u32(&full_bar[kb % STAGES]), (kb / STAGES) & 1);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+  }
+}
+
+// ---- host side ----------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *m, TcMode mode, const TcOperand &op, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  const int eb = tc_elem_bytes(mode);
+  const int planes = tc_planes(mode);
+  cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)op.pitch * eb, (cuuint64_t)op.pitch * eb * op.rows};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt =
+      mode == TcMode::TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = enc(m, dt, 3, const_cast<void *>(op.base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int MODE, int BN>
+cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K,
+                   const TcEpilogue &epi, int *err, cudaStream_t s) {
+  using C = Cfg<MODE, BN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<MODE, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((M + C::BM - 1) / C::BM, (N + BN - 1) / BN);
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  k_tc_gemm<MODE, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, epi, err);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_bn(const TcOperand &A, const TcOperand &B, int M, int N, int K,
+                        const TcEpilogue &epi, int *err, cudaStream_t s) {
+  const TcMode mode = static_cast<TcMode>(MODE);
+  const int bn = N <= 64 ? 64 : (N <= 128 || MODE != 0 ? 128 : 256);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, mode, A, 128) || !make_map(&tb, mode, B, bn)) return cudaErrorInvalidValue;
+  if (bn == 64) return launch<MODE, 64>(ta, tb, M, N, K, epi, err, s);
+  if (bn == 128) return launch<MODE, 128>(ta, tb, M, N, K, epi, err, s);
+  if constexpr (MODE == 0) return launch<MODE, 256>(ta, tb, M, N, K, epi, err, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, int N, int K,
+                    const TcEpilogue &epi, int *err_flag, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0 || A.K != K || B.K != K || A.rows < M || B.rows < N) return cudaErrorInvalidValue;
+  if (A.pitch != tc_pitch(A.pitch, mode) || B.pitch != tc_pitch(B.pitch, mode) || A.pitch < K ||
+      B.pitch < K)
+    return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(A.base) & 15) || (reinterpret_cast<uintptr_t>(B.base) & 15))
+    return cudaErrorInvalidValue;
+  switch (mode) {
+    case TcMode::TF32: return dispatch_bn<0>(A, B, M, N, K, epi, err_flag, s);
+    case TcMode::BF16X3: return dispatch_bn<1>(A, B, M, N, K, epi, err_flag, s);
+    case TcMode::BF16X6: return dispatch_bn<2>(A, B, M, N, K, epi, err_flag, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hotrg

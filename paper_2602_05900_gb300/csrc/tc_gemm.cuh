@@ -1,0 +1,56 @@
+// tcgen05 / TMA GEMM for sm_103a: C = sum over products of A_p . B_q^T with
+// K-major operands in shared memory (128-byte swizzle), FP32 accumulation in
+// tensor memory, and an epilogue that writes through an (IdxMap, IdxMap) pair
+// into FP32, FP64 or split-BF16 planes.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace hotrg {
+
+// Operand arithmetic of a tensor-core GEMM.
+enum class TcMode : int {
+  TF32 = 0,     // one FP32 plane (pre-rounded to TF32), kind::tf32
+  BF16X3 = 1,   // two BF16 planes (hi, lo), products hh + hl + lh, kind::f16
+  BF16X6 = 2,   // three BF16 planes, products with plane-index sum <= 2 (0-based)
+};
+
+inline int tc_planes(TcMode m) { return m == TcMode::TF32 ? 1 : (m == TcMode::BF16X3 ? 2 : 3); }
+inline int tc_elem_bytes(TcMode m) { return m == TcMode::TF32 ? 4 : 2; }
+
+// Output format of the epilogue.
+enum class OutKind : int { F32 = 0, F64 = 1, BF16P = 2 };
+
+// A dense operand in global memory: `planes` planes of `rows` x `pitch`
+// elements (K contiguous), plane stride rows * pitch.  Only the first K
+// columns are read (the rest of each row is padding).
+struct TcOperand {
+  const void *base;
+  int rows, K, pitch;
+};
+
+struct TcEpilogue {
+  OutKind kind;
+  void *C;
+  long long plane_stride;  // elements between output planes (BF16P)
+  int planes;              // output planes (BF16P): 1, 2 or 3
+  bool round_tf32;         // F32 output feeds a TF32 operand: round to nearest TF32
+  IdxMap cm, cn;
+};
+
+// Launches one GEMM C(M x N) = A(M x K) . B(N x K)^T; returns a CUDA error
+// code (cudaErrorInvalidValue for unsupported shapes).
+cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, int N, int K,
+                    const TcEpilogue &epi, int *err_flag, cudaStream_t s);
+
+// Number of padded columns an operand row needs so that its byte pitch is a
+// multiple of 16 (the TMA stride rule).
+inline int tc_pitch(int K, TcMode m) {
+  const int q = 16 / tc_elem_bytes(m);
+  return ((K + q - 1) / q) * q;
+}
+
+}  // namespace hotrg

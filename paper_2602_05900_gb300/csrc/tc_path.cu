@@ -1,0 +1,230 @@
+// Tensor-core chain of the HOTRG step's contractions (TF32 / split BF16).
+//
+// Operands of every GEMM are dense K-major planes (TMA needs a unit-stride
+// K axis), so the step first gathers the permuted views of T and U it needs
+// into such planes (a1: small, D^4 elements each).  The GEMMs whose result
+// feeds the next GEMM (environment partials -> Gram combine, P -> Q, Q -> T')
+// write that result straight into the next GEMM's operand format through
+// their epilogue maps, so no D^5 tensor is ever permuted or converted in a
+// separate pass.
+#include <cuda_bf16.h>
+
+#include "tc_gemm.cuh"
+#include "tc_path.cuh"
+
+namespace hotrg {
+
+struct TcPath::Impl {
+  TcMode mode = TcMode::TF32;
+  cudaStream_t s = nullptr;
+  int planes = 1, eb = 4;
+  void *opT[4] = {};       // a2 operands: permuted views of T
+  void *part[4] = {};      // a2 outputs / a3 operands: [x][u] x [k][k']
+  void *opU5 = nullptr, *opT5 = nullptr, *opT6 = nullptr, *opU7 = nullptr;
+  void *P = nullptr, *Q = nullptr;
+  int *err = nullptr;
+  std::size_t capT = 0, capP = 0;  // elements per plane
+  ~Impl() {
+    for (void *p : opT) cudaFree(p);
+    for (void *p : part) cudaFree(p);
+    cudaFree(opU5);
+    cudaFree(opT5);
+    cudaFree(opT6);
+    cudaFree(opU7);
+    cudaFree(P);
+    cudaFree(Q);
+  }
+};
+
+namespace {
+
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+  return __uint_as_float(u);
+}
+
+// dst[p][r][k] (pitch columns, zero beyond K) = split_p(src[rm(r) + km(k)])
+template <int MODE>
+__global__ void k_gather(const double *src, int R, int K, int pitch, IdxMap rm, IdxMap km,
+                         void *dst, long long plane_stride) {
+  const long long total = (long long)R * pitch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / pitch), k = (int)(e % pitch);
+    const double v = (k < K) ? src[map_off(rm, r) + map_off(km, k)] : 0.0;
+    if constexpr (MODE == 0) {
+      static_cast<float *>(dst)[e] = tf32_rna(static_cast<float>(v));
+    } else {
+      constexpr int NP = MODE == 1 ? 2 : 3;
+      __nv_bfloat16 *d = static_cast<__nv_bfloat16 *>(dst);
+      double rem = v;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const __nv_bfloat16 t = __double2bfloat16(rem);
+        d[e + p * plane_stride] = t;
+        rem -= static_cast<double>(__bfloat162float(t));
+      }
+    }
+  }
+}
+
+int grid_for(long long count) {
+  long long b = (count + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+void *alloc(std::size_t bytes) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes + 256) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+}  // namespace
+
+TcPath::~TcPath() { delete impl_; }
+
+int TcPath::init(hotrg_prec prec, int D0, int D_cut, cudaStream_t s, int *err_flag) {
+  impl_ = new Impl();
+  Impl &I = *impl_;
+  I.mode = prec == HOTRG_TF32 ? TcMode::TF32 : (prec == HOTRG_BF16X3 ? TcMode::BF16X3 : TcMode::BF16X6);
+  I.s = s;
+  I.planes = tc_planes(I.mode);
+  I.eb = tc_elem_bytes(I.mode);
+  const long long Dm = D0 > D_cut ? D0 : D_cut;
+  // Per-plane capacities.  Rows are padded to a 16-byte pitch (at most 7 extra
+  // elements), so every operand fits (Dm^2 + 8)^2 elements and every D^5
+  // intermediate fits D_cut Dm^2 (Dm^2 + 8).
+  I.capT = (std::size_t)((Dm * Dm + 8) * (Dm * Dm + 8));
+  I.capP = (std::size_t)(D_cut * Dm * Dm * (Dm * Dm + 8));
+  const std::size_t bt = I.capT * I.planes * I.eb, bp = I.capP * I.planes * I.eb;
+  for (int i = 0; i < 4; ++i) {
+    if (!(I.opT[i] = alloc(bt))) return 2;
+    if (!(I.part[i] = alloc(bt))) return 2;
+  }
+  if (!(I.opU5 = alloc(bt)) || !(I.opT5 = alloc(bt)) || !(I.opT6 = alloc(bt)) ||
+      !(I.opU7 = alloc(bt)) || !(I.P = alloc(bp)) || !(I.Q = alloc(bp)))
+    return 2;
+  I.err = err_flag;
+  return 0;
+}
+
+static cudaError_t gather(const TcPath::Impl &I, const double *src, int R, int K, int pitch,
+                          IdxMap rm, IdxMap km, void *dst) {
+  const long long ps = (long long)R * pitch;
+  const int g = grid_for(ps);
+  switch (I.mode) {
+    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, R, K, pitch, rm, km, dst, ps); break;
+    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, R, K, pitch, rm, km, dst, ps); break;
+    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, R, K, pitch, rm, km, dst, ps); break;
+  }
+  return cudaGetLastError();
+}
+
+// Epilogue writing an operand-format result (next GEMM's A or B planes).
+static TcEpilogue operand_epilogue(const TcPath::Impl &I, void *dst, long long plane_stride,
+                                   IdxMap cm, IdxMap cn) {
+  TcEpilogue e{};
+  if (I.mode == TcMode::TF32) {
+    e.kind = OutKind::F32;
+    e.round_tf32 = true;
+  } else {
+    e.kind = OutKind::BF16P;
+    e.planes = I.planes;
+  }
+  e.C = dst;
+  e.plane_stride = plane_stride;
+  e.cm = cm;
+  e.cn = cn;
+  return e;
+}
+
+static TcEpilogue f64_epilogue(double *dst, IdxMap cm, IdxMap cn) {
+  TcEpilogue e{};
+  e.kind = OutKind::F64;
+  e.C = dst;
+  e.planes = 1;
+  e.cm = cm;
+  e.cn = cn;
+  return e;
+}
+
+int TcPath::environment(const double *T, int D, int E, long long sx, long long sxp, long long sy,
+                        long long syp, double *, double *, double *, double *, double *GL,
+                        double *GR) {
+  Impl &I = *impl_;
+  const int DE = D * E, E2 = E * E, D2 = D * D;
+  const int p2 = tc_pitch(DE, I.mode);   // a2 operand pitch
+  const int p3 = tc_pitch(E2, I.mode);   // a3 operand pitch
+  if ((std::size_t)DE * p2 > I.capT || (std::size_t)D2 * p3 > I.capT) return 1;
+  const IdxMap rows[4] = {map2(E, syp, sx), map2(E, sy, sx), map2(E, syp, sxp), map2(E, sy, sxp)};
+  const IdxMap reds[4] = {map2(E, sy, sxp), map2(E, syp, sxp), map2(E, sy, sx), map2(E, syp, sx)};
+  for (int i = 0; i < 4; ++i) {
+    if (gather(I, T, DE, DE, p2, rows[i], reds[i], I.opT[i]) != cudaSuccess) return 1;
+    // part[i][(x,u)][(k,k')]: rows m = (x, k), cols n = (u, k')
+    TcOperand op{I.opT[i], DE, DE, p2};
+    TcEpilogue ep = operand_epilogue(I, I.part[i], (long long)D2 * p3,
+                                     map2(E, E, (long long)D * p3), map2(E, 1, p3));
+    if (tc_gemm(I.mode, op, op, DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
+  }
+  const IdxMap gm = map2(D, D, (long long)D2 * D), gn = map2(D, 1, D2);
+  for (int side = 0; side < 2; ++side) {
+    TcOperand a{I.part[2 * side], D2, E2, p3};
+    TcOperand b{I.part[2 * side + 1], D2, E2, p3};
+    if (tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(side ? GR : GL, gm, gn), I.err, I.s) !=
+        cudaSuccess)
+      return 1;
+  }
+  return 0;
+}
+
+int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long long sx,
+                    long long sxp, long long sy, long long syp, double *Tout, IdxMap tm,
+                    IdxMap tn) {
+  Impl &I = *impl_;
+  const int n = D * D, DE = D * E, E2 = E * E;
+  const int p5 = tc_pitch(D, I.mode), p6 = tc_pitch(DE, I.mode), p7 = tc_pitch(n, I.mode);
+  if ((std::size_t)D * Dn * p5 > I.capT || (std::size_t)D * E2 * p5 > I.capT ||
+      (std::size_t)DE * p6 > I.capT || (std::size_t)Dn * p7 > I.capT ||
+      (std::size_t)Dn * DE * p6 > I.capP || (std::size_t)Dn * E2 * p7 > I.capP)
+    return 1;
+  // a1: operands of a5 (U and T views with the x1 axis as K), a6 (T view) and a7 (U^T)
+  if (gather(I, U, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5) != cudaSuccess) return 1;
+  if (gather(I, T, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5) != cudaSuccess)
+    return 1;
+  if (gather(I, T, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6) != cudaSuccess)
+    return 1;
+  if (gather(I, U, Dn, n, p7, map1(n), map1(1), I.opU7) != cudaSuccess) return 1;
+
+  // a5: P[(a,x1',y)][(x2,k)] = sum_x1 U[(x1 x2),a] T[x1,x1',y,k]; rows m = (x2,a), cols (x1',y,k)
+  {
+    TcOperand a{I.opU5, D * Dn, D, p5}, b{I.opT5, D * E2, D, p5};
+    const long long ps = (long long)Dn * DE * p6;
+    TcEpilogue ep = operand_epilogue(I, I.P, ps, map2(Dn, (long long)DE * p6, E),
+                                     map3(E, E, 1, p6, (long long)E * p6));
+    if (tc_gemm(I.mode, a, b, D * Dn, D * E2, D, ep, I.err, I.s) != cudaSuccess) return 1;
+  }
+  // a6: Q[(a,y,y')][(x1',x2')] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
+  {
+    TcOperand a{I.P, Dn * DE, DE, p6}, b{I.opT6, DE, DE, p6};
+    const long long ps = (long long)Dn * E2 * p7;
+    TcEpilogue ep = operand_epilogue(I, I.Q, ps,
+                                     map3(E, D, (long long)E * p7, D, (long long)E2 * p7),
+                                     map2(D, 1, p7));
+    if (tc_gemm(I.mode, a, b, Dn * DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
+  }
+  // a7: T'(m = (a,y,y'), b) = sum_{(x1',x2')} Q[m][(x1',x2')] U[(x1' x2'), b]
+  {
+    TcOperand a{I.Q, Dn * E2, n, p7}, b{I.opU7, Dn, n, p7};
+    if (tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn), I.err, I.s) !=
+        cudaSuccess)
+      return 1;
+  }
+  return 0;
+}
+
+}  // namespace hotrg

@@ -1,0 +1,75 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function the
+header declares, validates arguments without a GPU, and its host-side initial
+tensors match the oracle's (closed-form square root vs. eigendecomposition)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import hotrg as ref
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_05900_gb300 import build as b
+    b.build()
+    import paper_2602_05900_gb300 as pkg
+    return pkg.load()
+
+
+def test_header_declares_the_boundary():
+    from paper_2602_05900_gb300.capi import header_symbols
+    names = header_symbols()
+    for required in ["hotrg_create", "hotrg_step", "hotrg_free_energy", "hotrg_destroy",
+                     "hotrg_log_z_per_site", "hotrg_spectrum", "hotrg_step_info"]:
+        assert required in names
+
+
+def test_library_exports_every_header_symbol(lib):
+    from paper_2602_05900_gb300.capi import LIB_PATH, header_symbols
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = [s for s in header_symbols() if s not in exported]
+    assert not missing, missing
+    for s in header_symbols():
+        assert hasattr(lib, s)
+
+
+@pytest.mark.parametrize("beta,h", [(0.4406867935097715, 0.0), (0.44, 0.01), (0.3, -0.25), (1.3, 0.2)])
+def test_ising_tensor_matches_oracle(lib, beta, h):
+    import paper_2602_05900_gb300 as pkg
+    assert np.allclose(pkg.ising_tensor(beta, h), ref.ising_initial_tensor(beta, h),
+                       rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("q,beta", [(2, 0.7), (3, 1.0050525696307162), (4, 0.5), (5, 1.2)])
+def test_potts_tensor_matches_oracle(lib, q, beta):
+    import paper_2602_05900_gb300 as pkg
+    assert np.allclose(pkg.potts_tensor(q, beta), ref.potts_initial_tensor(q, beta),
+                       rtol=1e-13, atol=1e-13)
+
+
+def test_host_argument_validation(lib):
+    import paper_2602_05900_gb300 as pkg
+    from paper_2602_05900_gb300.capi import HOTRG_EINVAL
+    buf = np.zeros(16)
+    dp = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.hotrg_ising_tensor(-1.0, 0.0, dp) == HOTRG_EINVAL
+    assert lib.hotrg_ising_tensor(0.4, 0.0, None) == HOTRG_EINVAL
+    assert lib.hotrg_potts_tensor(1, 0.4, dp) == HOTRG_EINVAL
+    assert lib.hotrg_potts_tensor(17, 0.4, dp) == HOTRG_EINVAL
+    h = ctypes.c_void_p()
+    # invalid sizes and precisions are rejected before any device work
+    assert lib.hotrg_create(dp, 0, 8, 0, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_create(dp, 2, 65, 0, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_create(dp, 2, 8, 9, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_create(None, 2, 8, 0, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert h.value is None
+    assert lib.hotrg_step(None, 0) == HOTRG_EINVAL
+    lib.hotrg_destroy(None)   # NULL-safe
+    assert pkg.status_string(HOTRG_EINVAL) == "HOTRG_EINVAL"
