@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark: HOTRG RG-steps/s on GB300 through libhotrg's C ABI.
+
+One bench *step* is one full coarse-graining step (environments, FP64
+eigendecomposition, projection chain, rescale) at steady-state bond
+dimension Dx = Dy = D_cut of the named workload.  The job is brought to
+steady state first (the bond dimension grows from D0 = 2 over the first
+steps), then W warm-up steps run, then K steps are timed with CUDA events on
+the library's stream, each preceded by an L2 flush outside the events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision fp64|tf32|bf16x3|bf16x6] [--impl ours|reference]
+
+N > 1 (torchrun) runs N independent replicas, one per GPU (an RG step of
+one instance does not shard); the value is the total over ranks divided by
+the slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import CONFIGS  # noqa: E402
+
+METRIC = "HOTRG RG-steps/s at steady-state D=D_cut (TF32 tensor-core contractions, FP64 eig)"
+L2_FLUSH_BYTES = 512 << 20
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor throughput
+BF16_SPLIT_PRODUCTS = {"bf16x3": 3, "bf16x6": 6}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), d.get("hbm_gbs"), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+def golden(name):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
+    if os.path.exists(path):
+        return json.load(open(path)).get(name)
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def initial_tensor(pkg, cfg):
+    return pkg.ising_tensor(cfg.beta, cfg.h) if cfg.family == "ising" else pkg.potts_tensor(cfg.q, cfg.beta)
+
+
+def step_flops(D, E, Dn):
+    """Algorithmic flops of one step (each product counted once)."""
+    return (4 * 2 * D ** 3 * E ** 3 + 2 * 2 * D ** 4 * E ** 2 + 2 * Dn * D ** 3 * E ** 2
+            + 2 * Dn * D ** 3 * E ** 3 + 2 * Dn ** 2 * D ** 2 * E ** 2)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def steady_job(pkg, cfg, precision, stream):
+    """A context advanced until Dx = Dy = D_cut; returns (ctx, next direction)."""
+    h = pkg.Hotrg(initial_tensor(pkg, cfg), cfg.D_cut, precision, stream)
+    d = "x"
+    for _ in range(64):
+        dx, dy, _ = h.dims()
+        if dx == cfg.D_cut and dy == cfg.D_cut:
+            break
+        h.step(d)
+        d = "y" if d == "x" else "x"
+    return h, d
+
+
+def time_steps(torch, h, d, k, stream, flush):
+    """Per-step CUDA-event times (ms) of k steps, L2 flushed before each."""
+    times = []
+    for _ in range(k):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.step(d)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        d = "y" if d == "x" else "x"
+    return times, d
+
+
+def full_job_lnz(pkg, cfg, precision, stream):
+    with pkg.Hotrg(initial_tensor(pkg, cfg), cfg.D_cut, precision, stream) as h:
+        h.run(cfg.steps)
+        return h.ln_z_per_site()
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2602_05900_gb300 as pkg
+    pkg.load()   # fails loudly if the CUDA library was not built
+    torch.cuda.set_device(local)
+    cfg = CONFIGS[args.workload]
+    prec = args.precision or cfg.precision
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    h, d = steady_job(pkg, cfg, prec, stream)
+    _, d = time_steps(torch, h, d, args.warmup, stream, flush)
+    h.profile_enable(True)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times, d = time_steps(torch, h, d, args.steps, stream, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof = h.profile_read()
+    h.close()
+    total_ms = sum(times)
+    max_ms = reduce_max(total_ms, world)
+
+    D = cfg.D_cut
+    flops_step = step_flops(D, D, D)
+    value = world * args.steps / (max_ms / 1e3)
+    bf16_burst, bf16_sust, hbm, peak_src = peaks()
+
+    # dominant contraction kernel: the bond contraction Q = P.T (a6), one launch per step
+    q_ms = prof["ms"]["proj_q"] / max(1, prof["stage_launches"]["proj_q"])
+    q_flops = 2.0 * D ** 7
+    achieved = q_flops / (q_ms / 1e3) / 1e12
+    if prec == "tf32":
+        peak, peak_note = bf16_burst * TF32_PER_BF16, f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"
+    elif prec in BF16_SPLIT_PRODUCTS:
+        peak = bf16_burst / BF16_SPLIT_PRODUCTS[prec]
+        peak_note = f"{peak_src} bf16 burst / {BF16_SPLIT_PRODUCTS[prec]} products (algorithmic flops)"
+    else:
+        peak, peak_note = 1.25, "nominal FP64 (no measured FP64 peak)"
+    roofline = {"kernel": "k_tc_gemm a6 bond contraction Q=P.T" if prec != "fp64" else "k_gemm_f64 a6",
+                "bound": "tensor" if prec != "fp64" else "alu", "achieved": round(achieved, 2),
+                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_source": peak_note,
+                "flops_per_launch": q_flops, "ms_per_launch": round(q_ms, 5)}
+
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "RG-steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6", "fp64": "f64"}[prec],
+           "data": "synthetic (analytic Ising/Potts initial tensor; no dataset)",
+           "config": {"workload": cfg.name, "family": cfg.family, "beta": cfg.beta, "h": cfg.h,
+                      "q": cfg.q, "D_cut": D, "steady_state_D": D, "precision": prec,
+                      "eig": "fp64 cuSOLVER syevdx (top D'+1 pairs, both sides)",
+                      "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write) and "
+                            f"per-step working set > L2", "parallelism": f"replicas x{world}"},
+           "tflops": round(flops_step * world * args.steps / (max_ms / 1e3) / 1e12, 3),
+           "roofline": roofline,
+           "stage_ms_per_step": {k: round(v / max(1, prof["steps"]), 4) for k, v in prof["ms"].items()},
+           "gpu_launches": int(prof["launches"]),
+           "clocks": clk.summary()}
+    out["stage_share"] = {k: round(v / max(1e-9, sum(prof["ms"].values())), 4) for k, v in prof["ms"].items()}
+    out["eig_share"] = out["stage_share"]["eig"]
+
+    if rank == 0 and not args.quick:
+        # accuracy of the full job against the FP64 oracle (stored by tests/golden/make_oracle_values.py)
+        g = golden(cfg.name)
+        lz = full_job_lnz(pkg, cfg, prec, stream)
+        lz64 = full_job_lnz(pkg, cfg, "fp64", stream)
+        if g:
+            out["fe_rel_err_vs_fp64_oracle"] = abs(lz / g["ln_z_per_site"] - 1)
+            out["fp64_gpu_fe_rel_err_vs_oracle"] = abs(lz64 / g["ln_z_per_site"] - 1)
+        out["fe_rel_err_vs_fp64_gpu"] = abs(lz / lz64 - 1)
+        out["ln_z_per_site"] = lz
+        # speedup over the plain FP64 GPU path on the same steady-state steps
+        h64, d64 = steady_job(pkg, cfg, "fp64", stream)
+        t64, _ = time_steps(torch, h64, d64, max(2, min(args.steps, 4)), stream, flush)
+        h64.close()
+        v64 = len(t64) / (sum(t64) / 1e3)
+        out["fp64_gpu_value"] = round(v64, 4)
+        out["speedup_vs_fp64_gpu"] = round(value / world / v64, 3)
+        out["e2e"] = e2e(pkg, cfg, prec, torch)
+        out["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
+    return out
+
+
+def e2e(pkg, cfg, prec, torch):
+    """The whole job through the public API from host memory: host T0 -> create
+    (H2D) -> cfg.steps steps -> free energy (D2H); RG-steps/s over the job."""
+    best = None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T0 = initial_tensor(pkg, cfg)
+        with pkg.Hotrg(T0, cfg.D_cut, prec) as h:
+            h.run(cfg.steps)
+            h.free_energy(cfg.beta)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    d0 = cfg.q
+    h2d = d0 ** 4 * 8
+    d2h = 12 * cfg.steps + 4 + 44     # per step: eig status + error flag; create flag; final scalars
+    return {"value": round(cfg.steps / best, 4), "unit": "RG-steps/s",
+            "h2d_bytes_per_step": round(h2d / cfg.steps, 2), "d2h_bytes_per_step": round(d2h / cfg.steps, 2),
+            "note": f"full {cfg.steps}-step job incl. context creation and transient steps"}
+
+
+def cpu_baseline(cfg, budget_s=20.0, max_steps=8):
+    """The FP64 oracle, as it stands, on the host cores: steady-state steps of the
+    same workload until about budget_s seconds of CPU work."""
+    from oracle import hotrg as ref
+    T0 = ref.ising_initial_tensor(cfg.beta, cfg.h) if cfg.family == "ising" else ref.potts_initial_tensor(cfg.q, cfg.beta)
+    c0 = float(abs(T0).max())
+    T = T0 / c0
+    d = "x"
+    n_tr = 0
+    while not (T.shape[0] == cfg.D_cut and T.shape[2] == cfg.D_cut):
+        T = (ref.x_step if d == "x" else ref.y_step)(T, cfg.D_cut)[0]
+        d = "y" if d == "x" else "x"
+        n_tr += 1
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and (k < 1 or time.perf_counter() - t0 < budget_s):
+        T = (ref.x_step if d == "x" else ref.y_step)(T, cfg.D_cut)[0]
+        d = "y" if d == "x" else "x"
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(k / dt, 5), "unit": "RG-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{k} steady-state steps at D={cfg.D_cut} of {cfg.name} after {n_tr} transient "
+                      f"steps (NumPy/OpenBLAS FP64, {dt:.1f} s)"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    cfg = CONFIGS[args.workload]
+    if rank != 0:
+        return None
+    budget = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    # each step: one steady-state oracle step (a bounded sample of the workload)
+    base = cpu_baseline(cfg, budget_s=0.0, max_steps=args.warmup)   # warm-up steps (untimed value)
+    from oracle import hotrg as ref  # noqa: F401
+    timed = cpu_baseline(cfg, budget_s=budget * args.steps, max_steps=args.steps)
+    v = timed["value"]
+    return {"metric": METRIC, "value": v, "unit": "RG-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 / v, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+            "data": "synthetic (analytic Ising/Potts initial tensor; no dataset)",
+            "config": {"workload": cfg.name, "D_cut": cfg.D_cut, "precision": "fp64 (CPU oracle)",
+                       "warmup_sample": base["sample"]},
+            "cpu_baseline": timed,
+            "e2e": {"value": v, "unit": "RG-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="ising_044_d32", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU legs")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return
+        else:
+            import torch
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_ours(args, world, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl != "reference":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,42 @@ hotrg_status hotrg_get_isometry(hotrg_ctx *ctx, double *host_out, long long cap,
 /* Current bond dimensions (Dx, Dy) and number of steps taken. */
 hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
 
+/*
+ * Stage profiler (tracing, no effect on results).  Stages of one step
+ * (Sec. II.A splits the cost into contraction and SVD; the contraction is
+ * split further here):
+ *   HOTRG_ST_PREP     operand gathers of the tensor-core path (a1)
+ *   HOTRG_ST_ENV      environment partials A_L, B_L, A_R, B_R (a2)
+ *   HOTRG_ST_GRAM     Gram combine G_L, G_R and FP64 symmetrisation (a3)
+ *   HOTRG_ST_EIG      FP64 eigendecomposition and choice of U (a4)
+ *   HOTRG_ST_PROJ_P   P = U.T (a5)
+ *   HOTRG_ST_PROJ_Q   Q = P.T, the bond contraction (a6)
+ *   HOTRG_ST_PROJ_T   T' = Q.U (a7)
+ *   HOTRG_ST_RESCALE  max-norm, rescale and log-sum (a8)
+ * While enabled, every step records CUDA events around each stage on the
+ * context's stream.  hotrg_profile_read synchronises the stream and returns
+ * the device time per stage accumulated since the profiler was (re)enabled,
+ * the algorithmic flops per stage (each flop counted once: split products
+ * and zero padding are not counted), and the number of kernels the library
+ * itself launched (library-internal eigensolver kernels are not counted).
+ */
+enum {
+  HOTRG_ST_PREP = 0, HOTRG_ST_ENV, HOTRG_ST_GRAM, HOTRG_ST_EIG, HOTRG_ST_PROJ_P,
+  HOTRG_ST_PROJ_Q, HOTRG_ST_PROJ_T, HOTRG_ST_RESCALE, HOTRG_NSTAGES
+};
+
+typedef struct {
+  int steps;                      /* steps profiled                                  */
+  long long launches;             /* own kernel launches in those steps              */
+  long long stage_launches[HOTRG_NSTAGES];
+  double ms[HOTRG_NSTAGES];       /* accumulated device time per stage (ms)          */
+  double flops[HOTRG_NSTAGES];    /* accumulated algorithmic flops per stage         */
+} hotrg_profile_t;
+
+/* Enable (1) or disable (0) the profiler; enabling resets the accumulators. */
+hotrg_status hotrg_profile_enable(hotrg_ctx *ctx, int enable);
+hotrg_status hotrg_profile_read(hotrg_ctx *ctx, hotrg_profile_t *out);
+
 /* Release all resources of the context; NULL is accepted and ignored. */
 void hotrg_destroy(hotrg_ctx *ctx);
 

@@ -31,6 +31,16 @@ class StepInfo(ctypes.Structure):
                 ("cut_gap", ctypes.c_double), ("trace_G", ctypes.c_double)]
 
 
+STAGES = ["prep", "env", "gram", "eig", "proj_p", "proj_q", "proj_t", "rescale"]
+
+
+class Profile(ctypes.Structure):
+    """Mirror of ``hotrg_profile_t``."""
+    _fields_ = [("steps", ctypes.c_int), ("launches", ctypes.c_longlong),
+                ("stage_launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8),
+                ("flops", ctypes.c_double * 8)]
+
+
 class HotrgError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -55,6 +65,8 @@ _SIGS = {
     "hotrg_get_tensor": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_longlong, _ip]),
     "hotrg_get_isometry": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_longlong, _ip, _ip]),
     "hotrg_dims": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip]),
+    "hotrg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hotrg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "hotrg_destroy": (None, [ctypes.c_void_p]),
 }
 
@@ -180,6 +192,17 @@ class Hotrg:
         self._check(load().hotrg_get_isometry(self._h, _ptr(out), out.size, ctypes.byref(rows),
                                               ctypes.byref(cols)), "hotrg_get_isometry")
         return out.reshape(cols.value, rows.value).T.copy()   # column-major -> [row, col]
+
+    def profile_enable(self, on: bool = True):
+        self._check(load().hotrg_profile_enable(self._h, 1 if on else 0), "hotrg_profile_enable")
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        self._check(load().hotrg_profile_read(self._h, ctypes.byref(p)), "hotrg_profile_read")
+        return {"steps": p.steps, "launches": p.launches,
+                "stage_launches": {k: int(p.stage_launches[i]) for i, k in enumerate(STAGES)},
+                "ms": {k: float(p.ms[i]) for i, k in enumerate(STAGES)},
+                "flops": {k: float(p.flops[i]) for i, k in enumerate(STAGES)}}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -32,6 +32,14 @@ __host__ __device__ inline long long map_off(const IdxMap &m, long long i) {
   return i0 * m.s0 + i1 * m.s1 + i2 * m.s2;
 }
 
+// Stage boundaries and launch counts reported to the context's profiler.
+struct StageHook {
+  virtual void begin(int stage) = 0;
+  virtual void end(int stage) = 0;
+  virtual void launched(int stage, int n) = 0;
+  virtual ~StageHook() {}
+};
+
 // C(m, n) = sum_k A(m, k) * B(n, k) over mapped operands.
 struct MappedGemm {
   int M, N, K;

@@ -31,9 +31,96 @@ namespace {
 constexpr int kMaxSteps = 256;
 constexpr int kRecord = 8;  // side, eps_L, eps_R, cut_gap, trace_G, ln_c, -, -
 
+// Records CUDA events around each stage while enabled; the intervals are
+// resolved into milliseconds once the stream has passed them.
+class Profiler : public StageHook {
+ public:
+  cudaStream_t stream = nullptr;
+  bool on = false;
+  hotrg_profile_t acc{};
+  long long launches_total = 0;   // own launches, whether or not profiling is on
+
+  ~Profiler() {
+    for (auto &p : pending_) {
+      cudaEventDestroy(p.b);
+      cudaEventDestroy(p.e);
+    }
+    for (cudaEvent_t e : pool_) cudaEventDestroy(e);
+  }
+  void reset() {
+    collect(true);
+    acc = hotrg_profile_t{};
+  }
+  void begin(int stage) override {
+    if (!on) return;
+    open_[stage] = get();
+    if (open_[stage]) cudaEventRecord(open_[stage], stream);
+  }
+  void end(int stage) override {
+    if (!on || !open_[stage]) return;
+    cudaEvent_t e = get();
+    if (!e) return;
+    cudaEventRecord(e, stream);
+    pending_.push_back({stage, open_[stage], e});
+    open_[stage] = nullptr;
+  }
+  void launched(int stage, int n) override {
+    launches_total += n;
+    if (!on) return;
+    acc.launches += n;
+    acc.stage_launches[stage] += n;
+  }
+  void flops(int stage, double f) {
+    if (on) acc.flops[stage] += f;
+  }
+  // Resolve finished intervals (all of them if `all`, after a stream sync).
+  void collect(bool all) {
+    std::vector<Interval> keep;
+    for (auto &p : pending_) {
+      float ms = 0.f;
+      cudaError_t r = cudaEventElapsedTime(&ms, p.b, p.e);
+      if (r == cudaSuccess) {
+        acc.ms[p.stage] += ms;
+        pool_.push_back(p.b);
+        pool_.push_back(p.e);
+      } else if (r == cudaErrorNotReady && !all) {
+        keep.push_back(p);
+      } else {
+        (void)cudaGetLastError();
+        pool_.push_back(p.b);
+        pool_.push_back(p.e);
+      }
+    }
+    pending_.swap(keep);
+  }
+
+ private:
+  struct Interval {
+    int stage;
+    cudaEvent_t b, e;
+  };
+  cudaEvent_t get() {
+    if (!pool_.empty()) {
+      cudaEvent_t e = pool_.back();
+      pool_.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  std::vector<Interval> pending_;
+  std::vector<cudaEvent_t> pool_;
+  cudaEvent_t open_[HOTRG_NSTAGES] = {};
+};
+
 }  // namespace
 
 struct hotrg_ctx {
+  Profiler prof;
   cudaStream_t stream = nullptr;
   Eig eig;
   TcPath tc;
@@ -177,6 +264,7 @@ hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec, 
     return s;
   };
   c->stream = static_cast<cudaStream_t>(stream);
+  c->prof.stream = c->stream;
   c->D0 = D0;
   c->D_cut = D_cut;
   c->Dm = D0 > D_cut ? D0 : D_cut;
@@ -225,6 +313,7 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   if (dir != HOTRG_DIR_X && dir != HOTRG_DIR_Y) return HOTRG_EINVAL;
   if (c->nsteps >= kMaxSteps) return fail(c, HOTRG_ESTATE, "step limit reached");
   cudaStream_t st = c->stream;
+  Profiler &pf = c->prof;
 
   // ---- the step's view of the stored tensor T[x,x',y,y'] (shape dx,dx,dy,dy)
   const bool ydir = (dir == HOTRG_DIR_Y);
@@ -240,43 +329,58 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   const int step = c->nsteps;
   double *rec = c->records + (size_t)step * kRecord;
   double *spec = c->spectra + (size_t)step * (c->D_cut + 1);
+  const double fD = D, fE = E, fDn = Dn;
+  pf.flops(HOTRG_ST_ENV, 4.0 * 2.0 * fD * fD * fD * fE * fE * fE);
+  pf.flops(HOTRG_ST_GRAM, 2.0 * 2.0 * fD * fD * fD * fD * fE * fE);
+  pf.flops(HOTRG_ST_PROJ_P, 2.0 * fDn * fD * fD * fD * fE * fE);
+  pf.flops(HOTRG_ST_PROJ_Q, 2.0 * fDn * fD * fD * fD * fE * fE * fE);
+  pf.flops(HOTRG_ST_PROJ_T, 2.0 * fDn * fDn * fD * fD * fE * fE);
 
-  // ---- a2: environment partials, written as [x][xbar][k][k'] for the Gram combine
-  const IdxMap out_m = map2(E, E, (long long)D * E2), out_n = map2(E, 1, E2);
-  struct Part { double *dst; IdxMap row, red; };
-  const Part parts[4] = {
-      {c->AL, map2(E, syp, sx), map2(E, sy, sxp)},    // A_L[x1,k,u1,k']: sum over (x1', y)
-      {c->BL, map2(E, sy, sx), map2(E, syp, sxp)},    // B_L[x2,k,u2,k']: sum over (x2', y')
-      {c->AR, map2(E, syp, sxp), map2(E, sy, sx)},    // A_R[x1',k,u1',k']: sum over (x1, y)
-      {c->BR, map2(E, sy, sxp), map2(E, syp, sx)},    // B_R[x2',k,u2',k']: sum over (x2, y')
-  };
+  // ---- a2/a3: environments G_L, G_R ([x1][x2][u1][u2], FP64)
   const bool tc = (c->prec != HOTRG_FP64);
   if (tc) {
-    int r = c->tc.environment(c->T, D, E, sx, sxp, sy, syp, c->AL, c->BL, c->AR, c->BR, c->GL,
-                              c->GR);
-    if (r) return fail(c, HOTRG_ECUDA, "tensor-core environment chain failed");
+    if (c->tc.environment(c->T, D, E, sx, sxp, sy, syp, c->GL, c->GR, &pf))
+      return fail(c, HOTRG_ECUDA, "tensor-core environment chain failed");
   } else {
+    // partials written as [x][u][k][k'] for the Gram combine
+    const IdxMap out_m = map2(E, E, (long long)D * E2), out_n = map2(E, 1, E2);
+    struct Part { double *dst; IdxMap row, red; };
+    const Part parts[4] = {
+        {c->AL, map2(E, syp, sx), map2(E, sy, sxp)},    // A_L[x1,k,u1,k']: sum over (x1', y)
+        {c->BL, map2(E, sy, sx), map2(E, syp, sxp)},    // B_L[x2,k,u2,k']: sum over (x2', y')
+        {c->AR, map2(E, syp, sxp), map2(E, sy, sx)},    // A_R[x1',k,u1',k']: sum over (x1, y)
+        {c->BR, map2(E, sy, sxp), map2(E, syp, sx)},    // B_R[x2',k,u2',k']: sum over (x2, y')
+    };
+    pf.begin(HOTRG_ST_ENV);
     for (const Part &p : parts) {
       MappedGemm g{(int)DE, (int)DE, (int)DE, c->T, p.row, p.red, c->T, p.row, p.red, p.dst, out_m, out_n};
       CK_CUDA(c, gemm_f64(g, st));
     }
-    // ---- a3: Gram combine G[x1,x2,u1,u2] = sum_{k,k'} A[x1,u1,k,k'] B[x2,u2,k,k']
+    pf.launched(HOTRG_ST_ENV, 4);
+    pf.end(HOTRG_ST_ENV);
+    // G[x1,x2,u1,u2] = sum_{k,k'} A[x1,u1,k,k'] B[x2,u2,k,k']
+    pf.begin(HOTRG_ST_GRAM);
     const IdxMap gm = map2(D, D, D2 * D), gn = map2(D, 1, D2);
     MappedGemm gl{(int)D2, (int)D2, (int)E2, c->AL, map1(E2), map1(1), c->BL, map1(E2), map1(1), c->GL, gm, gn};
     MappedGemm gr{(int)D2, (int)D2, (int)E2, c->AR, map1(E2), map1(1), c->BR, map1(E2), map1(1), c->GR, gm, gn};
     CK_CUDA(c, gemm_f64(gl, st));
     CK_CUDA(c, gemm_f64(gr, st));
+    pf.launched(HOTRG_ST_GRAM, 2);
   }
   CK_CUDA(c, symmetrize_trace(c->GL, n, c->scal + 2, st));
   CK_CUDA(c, symmetrize_trace(c->GR, n, c->scal + 3, st));
+  pf.launched(HOTRG_ST_GRAM, 4);
+  pf.end(HOTRG_ST_GRAM);
 
   // ---- a4: FP64 eigendecomposition and choice of U
+  pf.begin(HOTRG_ST_EIG);
   int spec_n;
   if (n <= c->D_cut) {
     CK_CUDA(c, identity_isometry(c->U, n, st));
     if (int r = c->eig.values(c->GL, n, c->wL, 0))
       return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (values) failed");
     CK_CUDA(c, spectrum_no_cut(c->wL, n, c->scal + 2, rec, spec, st));
+    pf.launched(HOTRG_ST_EIG, 2);
     spec_n = n;
   } else {
     const int m = Dn + 1;
@@ -286,11 +390,14 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
       return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (right) failed");
     SelectArgs a{n, Dn, m, c->wL, c->wR, c->GL, c->GR, c->scal + 2, c->scal + 3, c->U, rec, spec};
     CK_CUDA(c, select_isometry(a, st));
+    pf.launched(HOTRG_ST_EIG, 1);
     spec_n = m;
   }
+  pf.end(HOTRG_ST_EIG);
   int hinfo[2] = {0, 0};
   CK_CUDA(c, cudaMemcpyAsync(hinfo, c->eig.d_info(), sizeof(hinfo), cudaMemcpyDeviceToHost, st));
   CK_CUDA(c, cudaStreamSynchronize(st));
+  pf.collect(false);
   if (hotrg_status fs = check_flag(c)) return fs;
   if (hinfo[0] != 0 || (n > c->D_cut && hinfo[1] != 0))
     return fail(c, HOTRG_EEIG, "eigensolver info = " + std::to_string(hinfo[0]) + ", " +
@@ -302,33 +409,46 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
                          : map3(E, E, (long long)Dn * Dn, (long long)E * Dn * Dn, Dn);
   const IdxMap tn = ydir ? map1(E2) : map1(1);
   if (tc) {
-    int r = c->tc.project(c->T, c->U, D, E, Dn, sx, sxp, sy, syp, c->Tn, tm, tn);
-    if (r) return fail(c, HOTRG_ECUDA, "tensor-core projection chain failed");
+    if (c->tc.project(c->T, c->U, D, E, Dn, sx, sxp, sy, syp, c->Tn, tm, tn, &pf))
+      return fail(c, HOTRG_ECUDA, "tensor-core projection chain failed");
   } else {
     // a5: P[a][x1'][y][x2][k] = sum_x1 U[(x1 x2), a] T[x1,x1',y,k]
+    pf.begin(HOTRG_ST_PROJ_P);
     MappedGemm g5{(int)(D * Dn), (int)(D * E2), D,
                   c->U, map2(Dn, n, 1), map1(D),
                   c->T, map3(E, E, syp, sy, sxp), map1(sx),
                   c->P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E)};
     CK_CUDA(c, gemm_f64(g5, st));
+    pf.launched(HOTRG_ST_PROJ_P, 1);
+    pf.end(HOTRG_ST_PROJ_P);
     // a6: Q[a][y][y'][x1'][x2'] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
+    pf.begin(HOTRG_ST_PROJ_Q);
     MappedGemm g6{(int)(Dn * DE), (int)DE, (int)DE,
                   c->P, map1(DE), map1(1),
                   c->T, map2(D, sxp, syp), map2(E, sy, sx),
                   c->Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2)};
     CK_CUDA(c, gemm_f64(g6, st));
+    pf.launched(HOTRG_ST_PROJ_Q, 1);
+    pf.end(HOTRG_ST_PROJ_Q);
     // a7: T'[(a,y,y'), b] = sum_{x1',x2'} Q[(a,y,y'),(x1',x2')] U[(x1' x2'), b]
+    pf.begin(HOTRG_ST_PROJ_T);
     MappedGemm g7{(int)(Dn * E2), Dn, (int)D2,
                   c->Q, map1(D2), map1(1),
                   c->U, map1(n), map1(1),
                   c->Tn, tm, tn};
     CK_CUDA(c, gemm_f64(g7, st));
+    pf.launched(HOTRG_ST_PROJ_T, 1);
+    pf.end(HOTRG_ST_PROJ_T);
   }
 
   // ---- a8: rescale and FP64 log-sum
+  pf.begin(HOTRG_ST_RESCALE);
   const long long count = (long long)Dn * Dn * E2;
   CK_CUDA(c, maxabs_scale_log(c->Tn, count, c->scal + 1, c->scal, ldexp(1.0, -(step + 1)),
                               rec + 5, c->err, st));
+  pf.launched(HOTRG_ST_RESCALE, 2);
+  pf.end(HOTRG_ST_RESCALE);
+  if (pf.on) pf.acc.steps += 1;
   double *tmp = c->T;
   c->T = c->Tn;
   c->Tn = tmp;
@@ -343,6 +463,24 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   inf.Dn = Dn;
   c->info.push_back(inf);
   c->spec_count.push_back(spec_n);
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_profile_enable(hotrg_ctx *c, int enable) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->status != HOTRG_OK) return c->status;
+  CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_profile_read(hotrg_ctx *c, hotrg_profile_t *out) {
+  if (!c || !out) return HOTRG_EINVAL;
+  if (c->status != HOTRG_OK) return c->status;
+  CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->prof.collect(true);
+  *out = c->prof.acc;
   return HOTRG_OK;
 }
 

@@ -154,8 +154,7 @@ static TcEpilogue f64_epilogue(double *dst, IdxMap cm, IdxMap cn) {
 }
 
 int TcPath::environment(const double *T, int D, int E, long long sx, long long sxp, long long sy,
-                        long long syp, double *, double *, double *, double *, double *GL,
-                        double *GR) {
+                        long long syp, double *GL, double *GR, StageHook *hook) {
   Impl &I = *impl_;
   const int DE = D * E, E2 = E * E, D2 = D * D;
   const int p2 = tc_pitch(DE, I.mode);   // a2 operand pitch
@@ -163,14 +162,22 @@ int TcPath::environment(const double *T, int D, int E, long long sx, long long s
   if ((std::size_t)DE * p2 > I.capT || (std::size_t)D2 * p3 > I.capT) return 1;
   const IdxMap rows[4] = {map2(E, syp, sx), map2(E, sy, sx), map2(E, syp, sxp), map2(E, sy, sxp)};
   const IdxMap reds[4] = {map2(E, sy, sxp), map2(E, syp, sxp), map2(E, sy, sx), map2(E, syp, sx)};
-  for (int i = 0; i < 4; ++i) {
+  hook->begin(HOTRG_ST_PREP);
+  for (int i = 0; i < 4; ++i)
     if (gather(I, T, DE, DE, p2, rows[i], reds[i], I.opT[i]) != cudaSuccess) return 1;
+  hook->launched(HOTRG_ST_PREP, 4);
+  hook->end(HOTRG_ST_PREP);
+  hook->begin(HOTRG_ST_ENV);
+  for (int i = 0; i < 4; ++i) {
     // part[i][(x,u)][(k,k')]: rows m = (x, k), cols n = (u, k')
     TcOperand op{I.opT[i], DE, DE, p2};
     TcEpilogue ep = operand_epilogue(I, I.part[i], (long long)D2 * p3,
                                      map2(E, E, (long long)D * p3), map2(E, 1, p3));
     if (tc_gemm(I.mode, op, op, DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
   }
+  hook->launched(HOTRG_ST_ENV, 4);
+  hook->end(HOTRG_ST_ENV);
+  hook->begin(HOTRG_ST_GRAM);
   const IdxMap gm = map2(D, D, (long long)D2 * D), gn = map2(D, 1, D2);
   for (int side = 0; side < 2; ++side) {
     TcOperand a{I.part[2 * side], D2, E2, p3};
@@ -179,12 +186,13 @@ int TcPath::environment(const double *T, int D, int E, long long sx, long long s
         cudaSuccess)
       return 1;
   }
-  return 0;
+  hook->launched(HOTRG_ST_GRAM, 2);
+  return 0;   // the driver closes the GRAM stage after symmetrising
 }
 
 int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long long sx,
                     long long sxp, long long sy, long long syp, double *Tout, IdxMap tm,
-                    IdxMap tn) {
+                    IdxMap tn, StageHook *hook) {
   Impl &I = *impl_;
   const int n = D * D, DE = D * E, E2 = E * E;
   const int p5 = tc_pitch(D, I.mode), p6 = tc_pitch(DE, I.mode), p7 = tc_pitch(n, I.mode);
@@ -193,14 +201,18 @@ int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long
       (std::size_t)Dn * DE * p6 > I.capP || (std::size_t)Dn * E2 * p7 > I.capP)
     return 1;
   // a1: operands of a5 (U and T views with the x1 axis as K), a6 (T view) and a7 (U^T)
+  hook->begin(HOTRG_ST_PREP);
   if (gather(I, U, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5) != cudaSuccess) return 1;
   if (gather(I, T, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5) != cudaSuccess)
     return 1;
   if (gather(I, T, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6) != cudaSuccess)
     return 1;
   if (gather(I, U, Dn, n, p7, map1(n), map1(1), I.opU7) != cudaSuccess) return 1;
+  hook->launched(HOTRG_ST_PREP, 4);
+  hook->end(HOTRG_ST_PREP);
 
   // a5: P[(a,x1',y)][(x2,k)] = sum_x1 U[(x1 x2),a] T[x1,x1',y,k]; rows m = (x2,a), cols (x1',y,k)
+  hook->begin(HOTRG_ST_PROJ_P);
   {
     TcOperand a{I.opU5, D * Dn, D, p5}, b{I.opT5, D * E2, D, p5};
     const long long ps = (long long)Dn * DE * p6;
@@ -208,7 +220,10 @@ int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long
                                      map3(E, E, 1, p6, (long long)E * p6));
     if (tc_gemm(I.mode, a, b, D * Dn, D * E2, D, ep, I.err, I.s) != cudaSuccess) return 1;
   }
+  hook->launched(HOTRG_ST_PROJ_P, 1);
+  hook->end(HOTRG_ST_PROJ_P);
   // a6: Q[(a,y,y')][(x1',x2')] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
+  hook->begin(HOTRG_ST_PROJ_Q);
   {
     TcOperand a{I.P, Dn * DE, DE, p6}, b{I.opT6, DE, DE, p6};
     const long long ps = (long long)Dn * E2 * p7;
@@ -217,13 +232,18 @@ int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long
                                      map2(D, 1, p7));
     if (tc_gemm(I.mode, a, b, Dn * DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
   }
+  hook->launched(HOTRG_ST_PROJ_Q, 1);
+  hook->end(HOTRG_ST_PROJ_Q);
   // a7: T'(m = (a,y,y'), b) = sum_{(x1',x2')} Q[m][(x1',x2')] U[(x1' x2'), b]
+  hook->begin(HOTRG_ST_PROJ_T);
   {
     TcOperand a{I.Q, Dn * E2, n, p7}, b{I.opU7, Dn, n, p7};
     if (tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn), I.err, I.s) !=
         cudaSuccess)
       return 1;
   }
+  hook->launched(HOTRG_ST_PROJ_T, 1);
+  hook->end(HOTRG_ST_PROJ_T);
   return 0;
 }
 

@@ -18,13 +18,11 @@ class TcPath {
   int init(hotrg_prec prec, int D0, int D_cut, cudaStream_t s, int *err_flag);
   // a2 + a3: environments G_L, G_R (FP64, [x1,x2,u1,u2]) of a Y step on the
   // strided view (sx, sxp, sy, syp) of T with fused dim D and contracted dim E.
-  // AL..BR are FP64 scratch buffers of at least (D E)^2 doubles each.
   int environment(const double *T, int D, int E, long long sx, long long sxp, long long sy,
-                  long long syp, double *AL, double *BL, double *AR, double *BR, double *GL,
-                  double *GR);
+                  long long syp, double *GL, double *GR, StageHook *hook);
   // a5 - a7: T'(m, b) = [U^T (T.T) U], written in FP64 through the maps (tm, tn).
   int project(const double *T, const double *U, int D, int E, int Dn, long long sx, long long sxp,
-              long long sy, long long syp, double *Tout, IdxMap tm, IdxMap tn);
+              long long sy, long long syp, double *Tout, IdxMap tm, IdxMap tn, StageHook *hook);
 
   struct Impl;
 

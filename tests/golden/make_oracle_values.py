@@ -1,0 +1,60 @@
+"""Write ``oracle_values.json``: FP64 oracle results for the benchmark workloads.
+
+Calls only ``oracle/`` and the workload parameters in ``workloads/``; the CUDA
+library is never imported.  Each entry holds ln Z / N after the workload's
+step count, the free energy per site, and the per-step ln c_n, discarded
+weights, side and normalised spectrum head of the chosen environment.
+
+    python tests/golden/make_oracle_values.py [name ...]
+
+Entries already present are kept unless named on the command line.
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import hotrg  # noqa: E402
+from workloads import CONFIGS  # noqa: E402
+
+OUT = os.path.join(HERE, "oracle_values.json")
+
+
+def initial(cfg):
+    if cfg.family == "ising":
+        return hotrg.ising_initial_tensor(cfg.beta, cfg.h)
+    return hotrg.potts_initial_tensor(cfg.q, cfg.beta)
+
+
+def compute(cfg):
+    t0 = time.time()
+    r = hotrg.run(initial(cfg), cfg.D_cut, cfg.steps)
+    lz = r.ln_z_per_site
+    return {
+        "family": cfg.family, "beta": cfg.beta, "h": cfg.h, "q": cfg.q, "D_cut": cfg.D_cut,
+        "steps": cfg.steps, "first": "x",
+        "ln_z_per_site": lz, "free_energy": -lz / cfg.beta,
+        "per_step": [{"dir": s.direction, "Dx": s.Dx, "Dy": s.Dy, "Dn": s.Dn, "ln_c": s.ln_c,
+                      "eps_L": s.eps_L, "eps_R": s.eps_R, "side": s.side,
+                      "cut_gap": s.cut_gap if s.cut_gap != float("inf") else None,
+                      "trace_G": s.trace_G, "spectrum_head": [float(v) for v in s.spectrum[:8]]}
+                     for s in r.steps],
+        "oracle_seconds": time.time() - t0,
+    }
+
+
+def main(names):
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    todo = names or [n for n in CONFIGS if n not in data]
+    for name in todo:
+        print(f"oracle: {name} ...", flush=True)
+        data[name] = compute(CONFIGS[name])
+        print(f"  ln Z/N = {data[name]['ln_z_per_site']:.16f} ({data[name]['oracle_seconds']:.0f} s)", flush=True)
+        json.dump(data, open(OUT, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
