@@ -87,6 +87,10 @@ typedef struct {
   double cut_gap;   /* (lambda_D' - lambda_{D'+1}) / lambda_1 of the chosen side, or
                        +inf when nothing is cut                                     */
   double trace_G;   /* Tr G_L (= ||M||_F^2)                                        */
+  int eig_path;     /* eigensolver used: 0 none (no cut), 1 direct Jacobi,
+                       2 subspace iteration, 3 library fallback (cuSOLVER syevdx)   */
+  int eig_iters;    /* subspace iterations (path 2)                                */
+  double eig_residual; /* max_i<=D' ||G u_i - lambda_i u_i|| / lambda_1 (path 2)    */
 } hotrg_step_info_t;
 
 /*
@@ -117,6 +121,12 @@ hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec,
  * One coarse-graining step in direction dir (Sec. II.A): environments, FP64
  * eigendecomposition and choice of U, projection T' = U^T (T.T) U, max-norm
  * rescale and log-sum update.  See the header comment for the synchronisation.
+ * The leading D'+1 eigenpairs of each environment come from a batched FP64
+ * eigensolver (both environments at once): for Dx^2 <= 96 a parallel two-sided
+ * Jacobi diagonalisation of the whole matrix (Sec. II.B, Eqs. 5-6), otherwise
+ * block subspace iteration with Rayleigh-Ritz steps solved by the same Jacobi
+ * method, stopped at a residual of 1e-12 relative to the largest eigenvalue;
+ * if that does not converge the step falls back to cuSOLVER's syevdx.
  */
 hotrg_status hotrg_step(hotrg_ctx *ctx, hotrg_dir dir);
 

@@ -28,7 +28,9 @@ class StepInfo(ctypes.Structure):
     _fields_ = [("dir", ctypes.c_int), ("Dx", ctypes.c_int), ("Dy", ctypes.c_int),
                 ("Dn", ctypes.c_int), ("side", ctypes.c_int), ("ln_c", ctypes.c_double),
                 ("eps_L", ctypes.c_double), ("eps_R", ctypes.c_double),
-                ("cut_gap", ctypes.c_double), ("trace_G", ctypes.c_double)]
+                ("cut_gap", ctypes.c_double), ("trace_G", ctypes.c_double),
+                ("eig_path", ctypes.c_int), ("eig_iters", ctypes.c_int),
+                ("eig_residual", ctypes.c_double)]
 
 
 STAGES = ["prep", "env", "gram", "eig", "proj_p", "proj_q", "proj_t", "rescale"]

@@ -69,7 +69,8 @@ cudaError_t scale_initial(double *T, long long count, double *scratch_max, doubl
 // of the top of each spectrum.
 struct SelectArgs {
   int n, Dn, m;               // matrix size, kept count, eigenpairs computed per side
-  const double *wL, *wR;      // ascending eigenvalues (m)
+  int desc;                   // 1: values/vectors in descending order, 0: ascending
+  const double *wL, *wR;      // eigenvalues (m)
   const double *vL, *vR;      // eigenvectors, column-major n x m
   const double *trL, *trR;    // traces of G_L, G_R
   double *U;                  // out: n x Dn column-major
@@ -77,7 +78,7 @@ struct SelectArgs {
   double *spectrum;           // out: normalised spectrum, Dn (+1 if cut) values
 };
 cudaError_t select_isometry(const SelectArgs &a, cudaStream_t s);
-cudaError_t spectrum_no_cut(const double *w_asc, int n, const double *trL, double *record,
+cudaError_t spectrum_no_cut(const double *w, int n, int desc, const double *trL, double *record,
                             double *spectrum, cudaStream_t s);
 
 }  // namespace hotrg

@@ -22,6 +22,7 @@ int Eig::init(cudaStream_t s) {
   if (cusolverDnSetStream(handle_, s) != CUSOLVER_STATUS_SUCCESS) return 1;
   if (cusolverDnCreateParams(&params_) != CUSOLVER_STATUS_SUCCESS) return 1;
   if (cudaMalloc(&d_info_, 2 * sizeof(int)) != cudaSuccess) return 2;
+  if (cudaMemsetAsync(d_info_, 0, 2 * sizeof(int), s) != cudaSuccess) return 1;
   return 0;
 }
 

@@ -1,0 +1,821 @@
+// Batched FP64 subspace-iteration eigensolver for the environments (see
+// eig_si.cuh).  GB300's FP64 rate is a few flops per clock per SM, so the
+// work is arranged for the whole GPU: the products with G, the Gram matrices
+// and the basis rotations are tall-skinny FP64 GEMMs spread over all SMs (the
+// two environments of a step run in the same launches), and only the small
+// m x m factorisations run on one CTA per problem.
+//
+// One iteration:  Y = G X  ->  X = orth(Y)  (shifted CholeskyQR, three passes)
+// Every few iterations a Rayleigh-Ritz step diagonalises H = X^T G X with the
+// parallel two-sided Jacobi method and rotates X, Y onto the Ritz vectors;
+// the iteration stops when ||G x_i - theta_i x_i|| <= tol * theta_0 for i < k.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include <cooperative_groups.h>
+
+#include "eig_si.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hotrg {
+namespace {
+
+constexpr int kSplitMax = 8;     // split-K partials of G X
+constexpr int kChunkMax = 256;   // row chunks of the Gram reduction
+constexpr int kRowsPerChunk = 16;
+constexpr int kCluster = 8;      // CTAs per Jacobi problem (one thread-block cluster)
+constexpr int kJacobiMaxSweeps = 40;
+constexpr int kCholThreads = 256;
+
+struct Ptrs { double *p[kSiMaxBatch]; };
+struct CPtrs { const double *p[kSiMaxBatch]; };
+
+// splitmix64 finaliser (Steele, Lea, Flood 2014) -> uniform double in [-1, 1)
+__device__ inline double hash_uniform(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return static_cast<double>(x >> 11) * 0x1.0p-52 - 1.0;
+}
+
+// GB300 executes FP64 square roots and divisions as long dependent instruction
+// sequences; on the latency-bound paths below they are replaced by an FP32
+// estimate refined with FP64 fused multiply-adds (Newton's method), which is
+// accurate to FP64 rounding after two steps.
+
+// 2^-e scaling factor with e the binary exponent of x (exact, x > 0 finite)
+__device__ inline double pow2_inv_of(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF) - 1023;
+  return __longlong_as_double((long long)(1023 - e) << 52);
+}
+
+// 1/sqrt(x) for x > 0 to FP64 accuracy: FP32 seed on a power-of-two scaled
+// argument, two Newton steps y <- y (3 - x y^2) / 2 in FP64.
+__device__ inline double rsqrt_fp64(double x) {
+  const double s = pow2_inv_of(x);                  // x s in [1, 2)
+  const double xs = x * s;
+  double y = (double)rsqrtf((float)xs);
+  y = y * fma(-0.5 * xs, y * y, 1.5);
+  y = y * fma(-0.5 * xs, y * y, 1.5);
+  // 1/sqrt(x) = (1/sqrt(x s)) sqrt(s); s is a power of two
+  const long long sb = __double_as_longlong(s);
+  const int es = (int)((sb >> 52) & 0x7FF) - 1023;
+  double root_s = (es & 1) ? 1.4142135623730951 : 1.0;
+  root_s *= __longlong_as_double((long long)(1023 + (es >> 1)) << 52);
+  return y * root_s;
+}
+
+__global__ void k_si_init(Ptrs X, CPtrs warm, int kw, int n, int m) {
+  const int z = blockIdx.z;
+  const long long total = (long long)n * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n);
+    double v;
+    if (warm.p[z] && j < kw) v = warm.p[z][e];
+    else v = hash_uniform(((unsigned long long)z << 56) ^ ((unsigned long long)j << 32) ^ (unsigned long long)(e % n));
+    X.p[z][e] = v;
+  }
+}
+
+// Out_s = G[rows i0.., cols in split s] . X[those rows, :]  (X, Out column-major n x m)
+__global__ void __launch_bounds__(256) k_si_gemm(CPtrs G, CPtrs X, Ptrs Out, int n, int m, int chunk) {
+  __shared__ double Gs[16][65];
+  __shared__ double Xs[16][kSiMaxBlock];
+  const int z = blockIdx.z;
+  const double *g = G.p[z];
+  const double *x = X.p[z];
+  double *out = Out.p[z] + (size_t)blockIdx.y * n * m;
+  const int i0 = blockIdx.x * 64;
+  const int k0 = blockIdx.y * chunk;
+  const int k1 = min(n, k0 + chunk);
+  const int t = threadIdx.x, r = t & 63, cg = t >> 6;
+  double acc[kSiMaxBlock / 4];
+#pragma unroll
+  for (int c = 0; c < kSiMaxBlock / 4; ++c) acc[c] = 0.0;
+  for (int kk = k0; kk < k1; kk += 16) {
+    for (int e = t; e < 64 * 16; e += 256) {
+      const int row = e >> 4, col = e & 15;
+      const int gi = i0 + row, gk = kk + col;
+      Gs[col][row] = (gi < n && gk < k1) ? g[(size_t)gi * n + gk] : 0.0;
+    }
+    for (int e = t; e < 16 * m; e += 256) {
+      const int j = e >> 4, col = e & 15;
+      const int gk = kk + col;
+      Xs[col][j] = (gk < k1) ? x[(size_t)j * n + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+      const double gv = Gs[l][r];
+#pragma unroll
+      for (int c = 0; c < kSiMaxBlock / 4; ++c) {
+        const int j = cg + 4 * c;
+        if (j < m) acc[c] = fma(gv, Xs[l][j], acc[c]);
+      }
+    }
+    __syncthreads();
+  }
+  const int i = i0 + r;
+  if (i < n) {
+#pragma unroll
+    for (int c = 0; c < kSiMaxBlock / 4; ++c) {
+      const int j = cg + 4 * c;
+      if (j < m) out[(size_t)j * n + i] = acc[c];
+    }
+  }
+}
+
+__global__ void k_si_sum_split(Ptrs part, Ptrs out, int S, long long nm) {
+  const int z = blockIdx.z;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += part.p[z][s * nm + e];
+    out.p[z][e] = v;
+  }
+}
+
+// Cp[c] = A[rows of chunk c]^T B[same rows]   (m x m, row-major a*m + b)
+__global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int n, int m) {
+  __shared__ double As[16][kSiMaxBlock + 1];
+  __shared__ double Bs[16][kSiMaxBlock + 1];
+  const int z = blockIdx.z, c = blockIdx.x;
+  const double *a = A.p[z];
+  const double *b = B.p[z];
+  const int r0 = c * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
+  const int ta = threadIdx.x >> 4, tb = threadIdx.x & 15;
+  constexpr int U = kSiMaxBlock / 16;   // 6 x 6 outputs per thread
+  double acc[U][U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+  for (int rr = r0; rr < r1; rr += 16) {
+    for (int e = threadIdx.x; e < 16 * m; e += 256) {
+      const int j = e >> 4, ii = e & 15;
+      const int row = rr + ii;
+      As[ii][j] = (row < r1) ? a[(size_t)j * n + row] : 0.0;
+      Bs[ii][j] = (row < r1) ? b[(size_t)j * n + row] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < 16; ++ii) {
+      double av[U], bv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) av[u] = As[ii][ta * U + u];
+#pragma unroll
+      for (int v = 0; v < U; ++v) bv[v] = Bs[ii][tb * U + v];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double *out = Cp.p[z] + (size_t)c * m * m;
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const int ia = ta * U + u, ib = tb * U + v;
+      if (ia < m && ib < m) out[ia * m + ib] = acc[u][v];
+    }
+}
+
+// C = sum over row chunks of the Gram partials (fixed order), symmetrised.
+__global__ void k_si_gram_reduce(CPtrs Cp, Ptrs C, int nchunks, int m) {
+  const int z = blockIdx.z;
+  const long long mm = (long long)m * m;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int a = e / m, b = e % m;
+    if (b < a) continue;
+    double v = 0.0, w = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+      v += Cp.p[z][c * mm + a * m + b];
+      w += Cp.p[z][c * mm + b * m + a];
+    }
+    const double sv = 0.5 * (v + w);
+    C.p[z][a * m + b] = sv;
+    C.p[z][b * m + a] = sv;
+  }
+}
+
+// Shifted, column-scaled Cholesky of a block's Gram matrix C and the rotation
+// W = diag(d) R^-1 (column-major) such that Y W is orthonormal:
+//   C_hat = diag(d) C diag(d) + shift I = R^T R,  d_j = 1 / sqrt(C_jj).
+__global__ void __launch_bounds__(kCholThreads) k_si_chol(CPtrs Cin, int m, double shift, Ptrs Wout,
+                                                          int *flag) {
+  extern __shared__ double sh[];
+  const int ld = m + 1;
+  double *C = sh;                 // m x ld, upper triangle -> R
+  double *Z = sh + m * ld;        // m x ld, R^-1 (upper)
+  double *d = Z + m * ld;         // m
+  double *rinv = d + m;           // m: 1 / R_jj
+  const int z = blockIdx.z;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) C[(e / m) * ld + e % m] = Cin.p[z][e];
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double cjj = C[j * ld + j];
+    d[j] = (cjj > 0.0 && isfinite(cjj)) ? rsqrt_fp64(cjj) : 1.0;   // 1 / column norm
+  }
+  __syncthreads();
+  for (int a = ty; a < m; a += 16)
+    for (int b = tx; b < m; b += 16) C[a * ld + b] = C[a * ld + b] * (d[a] * d[b]) + (a == b ? shift : 0.0);
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // right-looking Cholesky on the upper triangle
+  for (int j = 0; j < m; ++j) {
+    const double piv = C[j * ld + j];
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;
+    }
+    const double ri = rsqrt_fp64(piv);          // 1 / R_jj
+    __syncthreads();
+    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) C[j * ld + l] *= ri;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      C[j * ld + j] = piv * ri;
+      rinv[j] = ri;
+    }
+    for (int a = j + 1 + ty; a < m; a += 16)
+      for (int b = a + tx; b < m; b += 16) C[a * ld + b] -= C[j * ld + a] * C[j * ld + b];
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(flag, 1);
+    return;
+  }
+  // R^-1 by right-looking back substitution: Z = I, then for i = m-1 .. 0 scale
+  // row i by 1/R_ii and eliminate it from the rows above (depth m, not m^2)
+  for (int a = ty; a < m; a += 16)
+    for (int b = tx; b < m; b += 16) Z[a * ld + b] = (a == b) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int i = m - 1; i >= 0; --i) {
+    for (int b = i + threadIdx.x; b < m; b += blockDim.x) Z[i * ld + b] *= rinv[i];
+    __syncthreads();
+    for (int a = ty; a < i; a += 16)
+      for (int b = i + tx; b < m; b += 16) Z[a * ld + b] = fma(-C[a * ld + i], Z[i * ld + b], Z[a * ld + b]);
+    __syncthreads();
+  }
+  double *W = Wout.p[z];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int c = e / m, j = e % m;           // W[j + c m]
+    W[e] = (j <= c) ? Z[j * ld + c] * d[j] : 0.0;
+  }
+}
+
+// Parallel two-sided Jacobi on a symmetric m x m matrix (m even) by a cluster
+// of kCluster CTAs, laid out as the systolic scheme of Sec. II.B / Fig. 3.
+// The m/2 index pairs of a round are "slots"; slot I holds two whole rows of
+// the matrix (its top and bottom index) and belongs to one CTA (contiguous
+// slots per CTA).  A round: (1) each CTA computes the rotation of its slots
+// from the 2x2 diagonal blocks it holds and broadcasts (p, q, c, s) to the
+// cluster; (2) each CTA applies every column rotation to the rows it holds and
+// its own row rotations, which is M'_{IJ} = J_I^T M_{IJ} J_J for all blocks of
+// its rows (Eq. 6), and rotates its share of the rows of V; (3) rows move to
+// their next slot (tops one slot down, bottoms one slot up, turning at both
+// ends: the round-robin order in which every pair meets once per sweep).
+// Sweeps stop when no pair needs rotating, or after a sweep whose rotated
+// entries were all below 1e-8 relative (quadratic convergence).
+__device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &c, double &s) {
+  // solve h_pq t^2 + (h_qq - h_pp) t - h_pq = 0 for the smaller root (Golub &
+  // Van Loan's symmetric Schur decomposition) on a power-of-two scaled copy:
+  // FP32 estimate, then two Newton steps whose residual is evaluated in FP64
+  const double sc = pow2_inv_of(fmax(fabs(hpq), fmax(fabs(hpp), fabs(hqq))));
+  const double a = hpp * sc, b = hqq * sc, g = hpq * sc, diff = b - a;
+  const float fg = (float)g, fd = (float)diff;
+  float t32;
+  if (fabsf(fd) > 1e6f * fabsf(fg)) {
+    t32 = fg / fd;                                  // 1/(2 tau), tau = diff / (2 g)
+  } else {
+    const float tau = fd / (2.0f * fg);
+    t32 = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+  }
+  double t = (double)t32;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double F = fma(fma(g, t, diff), t, -g);   // g t^2 + diff t - g
+    const double dF = fma(2.0 * g, t, diff);
+    t -= F * (double)__frcp_rn((float)dF);
+  }
+  c = rsqrt_fp64(fma(t, t, 1.0));
+  s = t * c;
+}
+
+__global__ void __launch_bounds__(512) k_si_jacobi(CPtrs Cin, int m, Ptrs Wout, Ptrs theta, int *flag,
+                                                   int *sweeps) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int z = blockIdx.z;
+  extern __shared__ double sh[];
+  const int half = m / 2;
+  const int spc = (half + kCluster - 1) / kCluster;          // slots per CTA
+  const int s0 = rank * spc, s1 = min(half, s0 + spc);      // own slots [s0, s1)
+  const int vrows = (m + kCluster - 1) / kCluster;
+  const int v0 = rank * vrows, v1 = min(m, v0 + vrows);     // own rows of V
+  // rows[buf][slot - s0][0 = top, 1 = bottom][m]
+  double *rowsb = sh;
+  auto ROW = [&](int buf, int slot, int tb) { return rowsb + (((size_t)buf * spc + (slot - s0)) * 2 + tb) * m; };
+  double *V = rowsb + (size_t)2 * spc * 2 * m;              // vrows x m
+  double *ac = V + (size_t)vrows * m;                       // c of every slot
+  double *as = ac + half;                                   // s of every slot
+  int *ap = reinterpret_cast<int *>(as + half);             // p of every slot
+  int *aq = ap + half;                                      // q of every slot
+  double *diag = reinterpret_cast<double *>(aq + half);   // m diagonal entries (2 half ints: 8-byte aligned)
+  __shared__ int rotated;                        // this CTA's slots needed a rotation
+  __shared__ unsigned int maxrel_bits;           // largest h_pq^2 / (h_pp h_qq) they had
+  __shared__ unsigned int sweep_flags[2 * kCluster];   // per rank: (rotated, maxrel)
+
+  // round 0 layout: position j holds index j; slot I = positions (I, m-1-I)
+  for (int e = threadIdx.x; e < (s1 - s0) * 2 * m; e += blockDim.x) {
+    const int sl = s0 + e / (2 * m), tb = (e / m) & 1, c = e % m;
+    const int idx = tb == 0 ? sl : m - 1 - sl;
+    ROW(0, sl, tb)[c] = Cin.p[z][(size_t)idx * m + c];
+  }
+  for (int e = threadIdx.x; e < (v1 - v0) * m; e += blockDim.x) {
+    const int rl = e / m, c = e % m;
+    V[rl * m + c] = (v0 + rl == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+
+  int cur = 0, sweep = 0, r_global = 0;
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    if (threadIdx.x == 0) {
+      rotated = 0;
+      maxrel_bits = 0u;
+    }
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r, ++r_global) {
+      // (1) rotations of own slots; the indices follow the round-robin order
+      for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
+        const int rr = r_global % (m - 1);
+        const int u = (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1);
+        const int v = 1 + (m - 2 - sl + rr) % (m - 1);
+        const double *top = ROW(cur, sl, 0), *bot = ROW(cur, sl, 1);
+        const int p = min(u, v), q = max(u, v);
+        const double *rp = (u < v) ? top : bot, *rq = (u < v) ? bot : top;
+        const double hpp = rp[p], hqq = rq[q], hpq = rp[q];
+        double c = 1.0, sv = 0.0;
+        if (hpq * hpq > 1e-30 * fabs(hpp * hqq) && fabs(hpq) > 1e-300) {
+          const float den = fabsf((float)hpp * (float)hqq);
+          const float rel2 = den > 0.0f ? fminf(1.0f, (float)hpq * (float)hpq / den) : 1.0f;
+          atomicMax(&maxrel_bits, __float_as_uint(rel2));
+          jacobi_angle(hpp, hqq, hpq, c, sv);
+          rotated = 1;
+        }
+        for (int k = 0; k < kCluster; ++k) {
+          double *rac = cluster.map_shared_rank(ac, k);
+          double *ras = cluster.map_shared_rank(as, k);
+          int *rap = cluster.map_shared_rank(ap, k);
+          int *raq = cluster.map_shared_rank(aq, k);
+          rac[sl] = c;
+          ras[sl] = sv;
+          rap[sl] = p;
+          raq[sl] = q;
+        }
+      }
+      cluster.sync();
+      // (2a) every column rotation on the rows this CTA holds
+      const int nrow = (s1 - s0) * 2;
+      for (int e = threadIdx.x; e < nrow * half; e += blockDim.x) {
+        const int ri = e / half, J = e % half;
+        double *row = ROW(cur, s0 + (ri >> 1), ri & 1);
+        const int p = ap[J], q = aq[J];
+        const double x = row[p], y = row[q];
+        row[p] = ac[J] * x - as[J] * y;
+        row[q] = as[J] * x + ac[J] * y;
+      }
+      // V <- V J on the rows of V this CTA holds
+      for (int e = threadIdx.x; e < (v1 - v0) * half; e += blockDim.x) {
+        const int rl = e / half, J = e % half;
+        const int p = ap[J], q = aq[J];
+        const double x = V[rl * m + p], y = V[rl * m + q];
+        V[rl * m + p] = ac[J] * x - as[J] * y;
+        V[rl * m + q] = as[J] * x + ac[J] * y;
+      }
+      __syncthreads();
+      // (2b) row rotation of each own slot, written straight to the next slots;
+      // (3) tops move one slot down (slot 1's top to slot 0's bottom), bottoms one
+      // slot up (the last slot's bottom to its own top); slot 0's top stays.
+      double *nx[kCluster];
+#pragma unroll
+      for (int k = 0; k < kCluster; ++k) nx[k] = cluster.map_shared_rank(rowsb, k);
+      for (int e = threadIdx.x; e < (s1 - s0) * m; e += blockDim.x) {
+        const int sl = s0 + e / m, col = e % m;
+        const double *top = ROW(cur, sl, 0), *bot = ROW(cur, sl, 1);
+        const int p = ap[sl], q = aq[sl];
+        const int u = (sl == 0) ? 0 : 1 + (sl - 1 + r_global % (m - 1)) % (m - 1);
+        const bool top_is_p = (u == p);
+        const double *rp = top_is_p ? top : bot, *rq = top_is_p ? bot : top;
+        const double c = ac[sl], sv = as[sl];
+        double np = c * rp[col] - sv * rq[col];
+        double nq = sv * rp[col] + c * rq[col];
+        if (col == q) np = 0.0;      // the rotated pair is diagonal to rounding
+        if (col == p) nq = 0.0;
+        const double ntop = top_is_p ? np : nq, nbot = top_is_p ? nq : np;
+        // destinations in the next buffer
+        int dsl, dtb;
+        if (sl == 0) { dsl = 0; dtb = 0; }               // slot 0's top is fixed
+        else if (sl == 1) { dsl = 0; dtb = 1; }          // -> slot 0 bottom
+        else { dsl = sl - 1; dtb = 0; }
+        {
+          const int own = dsl / spc;
+          double *base = nx[own] + ((((size_t)1 - cur) * spc + (dsl - own * spc)) * 2 + dtb) * m;
+          base[col] = ntop;
+        }
+        if (sl == half - 1) { dsl = sl; dtb = 0; } else { dsl = sl + 1; dtb = 1; }
+        {
+          const int own = dsl / spc;
+          double *base = nx[own] + ((((size_t)1 - cur) * spc + (dsl - own * spc)) * 2 + dtb) * m;
+          base[col] = nbot;
+        }
+      }
+      cluster.sync();
+      cur ^= 1;
+    }
+    // cluster-wide sweep decision: every CTA publishes its flags into every
+    // CTA's table, then all reduce the same table
+    if (threadIdx.x < kCluster) {
+      unsigned int *tab = cluster.map_shared_rank(sweep_flags, (int)threadIdx.x);
+      tab[2 * rank] = (unsigned)rotated;
+      tab[2 * rank + 1] = maxrel_bits;
+    }
+    cluster.sync();
+    bool any = false;
+    float mx = 0.0f;
+    for (int k = 0; k < kCluster; ++k) {
+      any = any || sweep_flags[2 * k] != 0u;
+      mx = fmaxf(mx, __uint_as_float(sweep_flags[2 * k + 1]));
+    }
+    // quadratic convergence: once every rotated entry was below 1e-8 relative,
+    // what remains after this sweep is at rounding level
+    const bool stop = !any || mx < 1e-16f;
+    cluster.sync();   // the table is read by everyone before the next sweep rewrites it
+    if (stop) {
+      ++sweep;
+      break;
+    }
+  }
+  // diagonal: each CTA knows the index of every row it holds; gather all m values
+  {
+    const int rr = r_global % (m - 1);
+    for (int e = threadIdx.x; e < (s1 - s0) * 2; e += blockDim.x) {
+      const int sl = s0 + (e >> 1), tb = e & 1;
+      const int idx = tb == 0 ? ((sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1)) : 1 + (m - 2 - sl + rr) % (m - 1);
+      const double dv = ROW(cur, sl, tb)[idx];
+      for (int k = 0; k < kCluster; ++k) cluster.map_shared_rank(diag, k)[idx] = dv;
+    }
+  }
+  cluster.sync();
+  if (threadIdx.x == 0 && rank == 0) {
+    if (sweep >= kJacobiMaxSweeps) atomicExch(flag, 2);
+    atomicMax(sweeps, sweep);
+  }
+  // sort descending (rank of each diagonal entry, ties by index)
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double ti = diag[i];
+    int rk = 0;
+    for (int j = 0; j < m; ++j) {
+      const double tj = diag[j];
+      rk += (tj > ti) || (tj == ti && j < i);
+    }
+    if (rank == 0) theta.p[z][rk] = ti;
+    for (int row = v0; row < v1; ++row) Wout.p[z][(size_t)rk * m + row] = V[(row - v0) * m + i];
+  }
+  cluster.sync();   // no CTA leaves while others may still read its shared memory
+}
+
+// Out = A . W  (A, Out n x m column-major; W m x m column-major: W[j + c m])
+__global__ void __launch_bounds__(256) k_si_rotate(CPtrs A, CPtrs W, Ptrs Out, int n, int m) {
+  __shared__ double As[32][33];
+  __shared__ double Ws[32][33];
+  const int z = blockIdx.z;
+  const double *a = A.p[z];
+  const double *w = W.p[z];
+  const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j0 = 0; j0 < m; j0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int jj = e >> 5, ii = e & 31;
+      const int row = i0 + ii, j = j0 + jj;
+      As[jj][ii] = (row < n && j < m) ? a[(size_t)j * n + row] : 0.0;
+      const int cc = c0 + jj;          // Ws[j][c]: load W[j + cc m] along j
+      const int jw = j0 + ii;
+      Ws[ii][jj] = (jw < m && cc < m) ? w[(size_t)cc * m + jw] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) {
+      const double av = As[jj][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(av, Ws[jj][ty + 8 * u], acc[u]);
+    }
+    __syncthreads();
+  }
+  const int i = i0 + tx;
+  if (i < n) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + ty + 8 * u;
+      if (c < m) Out.p[z][(size_t)c * n + i] = acc[u];
+    }
+  }
+}
+
+// res[i] = ||Y_i - theta_i X_i|| / |theta_0|, i < k
+__global__ void k_si_residual(CPtrs X, CPtrs Y, CPtrs theta, Ptrs res, int n, int k) {
+  const int z = blockIdx.z, i = blockIdx.x;
+  const double th = theta.p[z][i];
+  const double *x = X.p[z] + (size_t)i * n;
+  const double *y = Y.p[z] + (size_t)i * n;
+  double v = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double d = y[r] - th * x[r];
+    v = fma(d, d, v);
+  }
+  __shared__ double part[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    res.p[z][i] = sqrt(s) / fabs(theta.p[z][0]);
+  }
+}
+
+// G (n x n) into an m x m zero-padded square (m = n or n + 1) for the direct Jacobi path.
+__global__ void k_si_copy_square(CPtrs G, Ptrs out, int n, int m) {
+  const int z = blockIdx.z;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int a = e / m, b = e % m;
+    out.p[z][e] = (a < n && b < n) ? G.p[z][a * n + b] : 0.0;
+  }
+}
+
+// X[:, c] = first n rows of W[:, c] for c < k
+__global__ void k_si_take(CPtrs W, Ptrs X, int n, int m, int k) {
+  const int z = blockIdx.z;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += gridDim.x * blockDim.x) {
+    const int c = e / n, r = e % n;
+    X.p[z][(size_t)c * n + r] = W.p[z][(size_t)c * m + r];
+  }
+}
+
+// ---- host helpers ----
+
+struct Layout {
+  int S, NC, m;
+  long long nm, mm;
+  long long per;   // doubles per problem
+};
+
+Layout layout(int P, int n, int m) {
+  Layout L;
+  L.nm = (long long)n * m;
+  L.mm = (long long)m * m;
+  L.m = m;
+  const int tiles = (n + 63) / 64;
+  L.S = std::max(1, std::min(kSplitMax, (2 * 152 + tiles * P - 1) / std::max(1, tiles * P)));
+  while (L.S > 1 && (n + L.S - 1) / L.S < 64) --L.S;
+  L.NC = std::min(kChunkMax, (n + kRowsPerChunk - 1) / kRowsPerChunk);
+  L.per = L.nm * (2 + kSplitMax) + L.mm * (kChunkMax + 2) + 2 * m + 64;
+  return L;
+}
+
+struct Bufs {
+  double *Y[kSiMaxBatch], *Z[kSiMaxBatch], *Yp[kSiMaxBatch], *Cp[kSiMaxBatch], *C[kSiMaxBatch];
+  double *W[kSiMaxBatch], *res[kSiMaxBatch];
+  int *flag, *sweeps;
+};
+
+// per problem: Y, Z (n m each) | split partials (kSplitMax n m) | Gram partials
+// (kChunkMax m m) | C (m m) | W (m m) | res (m)
+Bufs carve(double *work, int P, const Layout &L) {
+  Bufs B{};
+  for (int p = 0; p < P; ++p) {
+    double *base = work + p * L.per;
+    B.Y[p] = base;
+    B.Z[p] = base + L.nm;
+    B.Yp[p] = base + 2 * L.nm;
+    B.Cp[p] = base + (2 + kSplitMax) * L.nm;
+    B.C[p] = B.Cp[p] + kChunkMax * L.mm;
+    B.W[p] = B.C[p] + L.mm;
+    B.res[p] = B.W[p] + L.mm;
+  }
+  B.flag = reinterpret_cast<int *>(work + P * L.per);
+  B.sweeps = B.flag + 2;
+  return B;
+}
+
+template <typename T>
+CPtrs cp_of(T *const *a, int P) {
+  CPtrs c{};
+  for (int p = 0; p < P; ++p) c.p[p] = a[p];
+  return c;
+}
+Ptrs p_of(double *const *a, int P) {
+  Ptrs c{};
+  for (int p = 0; p < P; ++p) c.p[p] = a[p];
+  return c;
+}
+
+size_t jacobi_smem(int m) {
+  const int half = m / 2;
+  const int spc = (half + kCluster - 1) / kCluster, vrows = (m + kCluster - 1) / kCluster;
+  return ((size_t)2 * spc * 2 * m + (size_t)vrows * m + 2 * half + m) * sizeof(double) +
+         (size_t)(2 * half + 2) * sizeof(int) + 64;
+}
+size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
+
+cudaError_t set_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e;
+  const int big = 200 * 1024;
+  if ((e = cudaFuncSetAttribute(k_si_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
+      (e = cudaFuncSetAttribute(k_si_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  done = true;
+  return cudaSuccess;
+}
+
+int grid_1d(long long count) {
+  long long b = (count + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(b, 152 * 4));
+}
+
+cudaError_t launch_jacobi(CPtrs C, int m, Ptrs W, Ptrs theta, int *flag, int *sweeps, int P,
+                          cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(kCluster, 1, P);
+  cfg.blockDim = dim3(512, 1, 1);
+  cfg.dynamicSmemBytes = jacobi_smem(m);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_si_jacobi, C, m, W, theta, flag, sweeps);
+}
+
+}  // namespace
+
+long long si_workspace_doubles(int P, int n, int m) {
+  return layout(P, n, m).per * P + 64;
+}
+
+cudaError_t jacobi_full(const SiBatch &b, double *work, cudaStream_t s, long long *launches) {
+  cudaError_t e = set_attrs();
+  if (e) return e;
+  const int n = b.n, P = b.P;
+  int m = n + (n & 1);              // the round-robin pairing needs an even size
+  if (m < 4) m = 4;                 // and at least two pairs
+  if (m > kSiMaxBlock || b.k > n) return cudaErrorInvalidValue;
+  const Layout L = layout(P, n, m);
+  Bufs B = carve(work, P, L);
+  if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
+  k_si_copy_square<<<dim3(grid_1d((long long)m * m), 1, P), 256, 0, s>>>(cp_of(b.G, P), p_of(B.C, P), n, m);
+  if ((e = launch_jacobi(cp_of(B.C, P), m, p_of(B.W, P), p_of(b.theta, P), B.flag, B.sweeps, P, s)))
+    return e;
+  k_si_take<<<dim3(grid_1d((long long)n * b.k), 1, P), 256, 0, s>>>(cp_of(B.W, P), p_of(b.X, P), n, m, b.k);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, cudaStream_t s,
+                     SiResult *res, long long *launches) {
+  cudaError_t e = set_attrs();
+  if (e) return e;
+  const int P = b.P, n = b.n, m = b.m, k = b.k;
+  if (P < 1 || P > kSiMaxBatch || m > kSiMaxBlock || m > n || k > m || (m & 1))
+    return cudaErrorInvalidValue;
+  const Layout L = layout(P, n, m);
+  Bufs B = carve(work, P, L);
+  double *X[kSiMaxBatch], *Y[kSiMaxBatch], *Z[kSiMaxBatch];
+  for (int p = 0; p < P; ++p) {
+    X[p] = b.X[p];
+    Y[p] = B.Y[p];
+    Z[p] = B.Z[p];
+  }
+  const dim3 gz(1, 1, P);
+  const dim3 grot((n + 31) / 32, (m + 31) / 32, P);
+  const int chunk = ((n + L.S - 1) / L.S + 15) / 16 * 16;
+  const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16;
+  long long nl = 0;
+
+  auto gemm = [&](double *const *src, double *const *dst) {
+    if (L.S == 1) {
+      k_si_gemm<<<dim3((n + 63) / 64, 1, P), 256, 0, s>>>(cp_of(b.G, P), cp_of(src, P), p_of(dst, P), n, m, chunk);
+      nl += 1;
+    } else {
+      k_si_gemm<<<dim3((n + 63) / 64, L.S, P), 256, 0, s>>>(cp_of(b.G, P), cp_of(src, P), p_of(B.Yp, P), n, m, chunk);
+      k_si_sum_split<<<dim3(grid_1d(L.nm), 1, P), 256, 0, s>>>(p_of(B.Yp, P), p_of(dst, P), L.S, L.nm);
+      nl += 2;
+    }
+  };
+  // C = A^T B (m x m), symmetrised
+  auto gram = [&](double *const *A, double *const *Bm) {
+    k_si_gram<<<dim3(L.NC, 1, P), 256, 0, s>>>(cp_of(A, P), cp_of(Bm, P), p_of(B.Cp, P), n, m);
+    k_si_gram_reduce<<<dim3(grid_1d(L.mm), 1, P), 256, 0, s>>>(cp_of(B.Cp, P), p_of(B.C, P), L.NC, m);
+    nl += 2;
+  };
+  // one CholeskyQR pass: dst = src diag(1/d) R^-1
+  auto cholqr = [&](double *const *src, double *const *dst, double sh) {
+    gram(src, src);
+    k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(cp_of(B.C, P), m, sh, p_of(B.W, P), B.flag);
+    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.W, P), p_of(dst, P), n, m);
+    nl += 2;
+  };
+  // dst = orth(src) by shifted CholeskyQR3: src -> tmp -> src -> dst
+  auto orth = [&](double **src, double **tmp, double **dst) {
+    cholqr(src, tmp, shift);
+    cholqr(tmp, src, 0.0);
+    cholqr(src, dst, 0.0);
+  };
+
+  if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
+  k_si_init<<<dim3(grid_1d(L.nm), 1, P), 256, 0, s>>>(p_of(X, P), cp_of(b.warm, P), b.kw, n, m);
+  nl += 1;
+  orth(X, Z, Y);                    // orthonormal start in Y
+  for (int p = 0; p < P; ++p) std::swap(X[p], Y[p]);
+
+  res->converged = false;
+  res->rr = 0;
+  res->residual = INFINITY;
+  int it = 0;
+  int next_check = 3;
+  std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
+  while (it < max_iter) {
+    gemm(X, Y);                     // Y = G X
+    ++it;
+    if (it >= next_check || it == max_iter) {
+      gram(X, Y);                   // H = X^T G X
+      if ((e = launch_jacobi(cp_of(B.C, P), m, p_of(B.W, P), p_of(b.theta, P), B.flag, B.sweeps, P, s)))
+        return e;
+      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(X, P), cp_of(B.W, P), p_of(Z, P), n, m);
+      for (int p = 0; p < P; ++p) std::swap(X[p], Z[p]);
+      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(Y, P), cp_of(B.W, P), p_of(Z, P), n, m);
+      for (int p = 0; p < P; ++p) std::swap(Y[p], Z[p]);
+      k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(cp_of(X, P), cp_of(Y, P), cp_of(b.theta, P), p_of(B.res, P), n, k);
+      nl += 4;
+      ++res->rr;
+      for (int p = 0; p < P; ++p) {
+        if ((e = cudaMemcpyAsync(hres.data() + (size_t)p * k, B.res[p], sizeof(double) * k,
+                                 cudaMemcpyDeviceToHost, s)))
+          return e;
+        if ((e = cudaMemcpyAsync(hth.data() + (size_t)p * m, b.theta[p], sizeof(double) * m,
+                                 cudaMemcpyDeviceToHost, s)))
+          return e;
+      }
+      int hflag[2];
+      if ((e = cudaMemcpyAsync(hflag, B.flag, sizeof(hflag), cudaMemcpyDeviceToHost, s))) return e;
+      if ((e = cudaStreamSynchronize(s))) return e;
+      double worst = 0.0;
+      for (double v : hres) worst = std::max(worst, std::isfinite(v) ? v : INFINITY);
+      res->residual = worst;
+      if (hflag[0]) break;          // factorisation breakdown: let the caller fall back
+      if (worst <= tol) {
+        res->converged = true;
+        break;
+      }
+      // Errors in the wanted Ritz pairs shrink by about theta_m / theta_k per
+      // iteration: schedule the next check where that predicts convergence.
+      double rho = 0.0;
+      for (int p = 0; p < P; ++p) {
+        const double tk = fabs(hth[(size_t)p * m + k - 1]), tm = fabs(hth[(size_t)p * m + m - 1]);
+        rho = std::max(rho, tk > 0.0 ? tm / tk : 1.0);
+      }
+      int need = 2;
+      if (rho > 0.0 && rho < 0.9 && std::isfinite(worst) && worst > 0.0)
+        need = (int)std::ceil(std::log(tol / worst) / std::log(rho)) + 1;
+      next_check = it + std::max(1, std::min(need, 8));
+    }
+    orth(Y, Z, X);                  // X = orth(G X)
+  }
+  res->iterations = it;
+  // the Ritz vectors must end in the caller's X buffers
+  for (int p = 0; p < P; ++p)
+    if (X[p] != b.X[p] &&
+        (e = cudaMemcpyAsync(b.X[p], X[p], sizeof(double) * L.nm, cudaMemcpyDeviceToDevice, s)))
+      return e;
+  *launches += nl;
+  return cudaGetLastError();
+}
+
+}  // namespace hotrg

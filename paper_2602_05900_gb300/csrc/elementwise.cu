@@ -114,27 +114,30 @@ __global__ void k_select(SelectArgs a) {
   __shared__ int s_side;
   __shared__ int s_arg;
   const int col = blockIdx.x;
+  // i-th largest eigenvalue / its vector, whatever order the solver returned
+  auto val = [&](const double *w, int i) { return a.desc ? w[i] : w[a.m - 1 - i]; };
+  auto vecidx = [&](int i) { return a.desc ? i : a.m - 1 - i; };
   if (threadIdx.x == 0) {
     double sumL = 0.0, sumR = 0.0;
-    for (int i = 0; i < a.Dn; ++i) {          // the Dn largest of m ascending values
-      sumL += a.wL[a.m - 1 - i];
-      sumR += a.wR[a.m - 1 - i];
+    for (int i = 0; i < a.Dn; ++i) {
+      sumL += val(a.wL, i);
+      sumR += val(a.wR, i);
     }
     const double epsL = *a.trL - sumL, epsR = *a.trR - sumR;
     s_side = (epsL <= epsR) ? 0 : 1;
     if (col == 0) {
       const double *w = s_side == 0 ? a.wL : a.wR;
-      const double l1 = w[a.m - 1];
+      const double l1 = val(w, 0);
       a.record[0] = (double)s_side;
       a.record[1] = epsL;
       a.record[2] = epsR;
-      a.record[3] = (a.m > a.Dn) ? (w[a.m - a.Dn] - w[a.m - a.Dn - 1]) / l1 : INFINITY;
+      a.record[3] = (a.m > a.Dn) ? (val(w, a.Dn - 1) - val(w, a.Dn)) / l1 : INFINITY;
       a.record[4] = *a.trL;
-      for (int i = 0; i < a.m; ++i) a.spectrum[i] = w[a.m - 1 - i] / l1;
+      for (int i = 0; i < a.m; ++i) a.spectrum[i] = val(w, i) / l1;
     }
   }
   __syncthreads();
-  const double *v = (s_side == 0 ? a.vL : a.vR) + (long long)(a.m - 1 - col) * a.n;
+  const double *v = (s_side == 0 ? a.vL : a.vR) + (long long)vecidx(col) * a.n;
   // sign convention: the component of largest magnitude (first on ties) is positive
   double best = -1.0;
   int arg = 0;
@@ -168,16 +171,16 @@ __global__ void k_select(SelectArgs a) {
   for (int i = threadIdx.x; i < a.n; i += blockDim.x) u[i] = sg * v[i];
 }
 
-__global__ void k_spectrum_no_cut(const double *w, int n, const double *trL, double *record,
-                                  double *spectrum) {
+__global__ void k_spectrum_no_cut(const double *w, int n, int desc, const double *trL,
+                                  double *record, double *spectrum) {
   if (threadIdx.x == 0) {
-    const double l1 = w[n - 1];
+    const double l1 = desc ? w[0] : w[n - 1];
     record[0] = -1.0;
     record[1] = 0.0;
     record[2] = 0.0;
     record[3] = INFINITY;
     record[4] = *trL;
-    for (int i = 0; i < n; ++i) spectrum[i] = w[n - 1 - i] / l1;
+    for (int i = 0; i < n; ++i) spectrum[i] = (desc ? w[i] : w[n - 1 - i]) / l1;
   }
 }
 
@@ -228,9 +231,9 @@ cudaError_t select_isometry(const SelectArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t spectrum_no_cut(const double *w_asc, int n, const double *trL, double *record,
+cudaError_t spectrum_no_cut(const double *w, int n, int desc, const double *trL, double *record,
                             double *spectrum, cudaStream_t s) {
-  k_spectrum_no_cut<<<1, 32, 0, s>>>(w_asc, n, trL, record, spectrum);
+  k_spectrum_no_cut<<<1, 32, 0, s>>>(w, n, desc, trL, record, spectrum);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@
 #include "../../include/hotrg.h"
 #include "common.cuh"
 #include "eig.cuh"
+#include "eig_si.cuh"
 #include "tc_path.cuh"
 
 using namespace hotrg;
@@ -141,6 +142,12 @@ struct hotrg_ctx {
   double *spectra = nullptr;   // kMaxSteps x (D_cut + 1)
   std::vector<hotrg_step_info_t> info;
   std::vector<int> spec_count;
+  // own FP64 eigensolver: workspace, Ritz vectors / values of both sides, and the
+  // last isometry per direction (start vectors of the next step in that direction)
+  double *si_work = nullptr;
+  double *XL = nullptr, *XR = nullptr, *thL = nullptr, *thR = nullptr;
+  double *Uprev[2] = {nullptr, nullptr};
+  int nprev[2] = {0, 0}, kprev[2] = {0, 0};
 
   hotrg_status status = HOTRG_OK;
   std::string msg;
@@ -283,6 +290,15 @@ hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec, 
       (s = dalloc(c, &c->records, (size_t)kMaxSteps * kRecord)) ||
       (s = dalloc(c, &c->spectra, (size_t)kMaxSteps * (D_cut + 1))))
     return bail(s);
+  {
+    const int nsi = (int)(nmax > kSiMaxBlock + 1 ? nmax : kSiMaxBlock + 1);
+    if ((s = dalloc(c, &c->si_work, (size_t)si_workspace_doubles(2, nsi, kSiMaxBlock))) ||
+        (s = dalloc(c, &c->XL, (size_t)nsi * kSiMaxBlock)) ||
+        (s = dalloc(c, &c->XR, (size_t)nsi * kSiMaxBlock)) || (s = dalloc(c, &c->thL, kSiMaxBlock)) ||
+        (s = dalloc(c, &c->thR, kSiMaxBlock)) || (s = dalloc(c, &c->Uprev[0], nmax * D_cut)) ||
+        (s = dalloc(c, &c->Uprev[1], nmax * D_cut)))
+      return bail(s);
+  }
   if (prec == HOTRG_FP64) {
     if ((s = dalloc(c, &c->P, p5)) || (s = dalloc(c, &c->Q, p5))) return bail(s);
   } else {
@@ -375,23 +391,80 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   // ---- a4: FP64 eigendecomposition and choice of U
   pf.begin(HOTRG_ST_EIG);
   int spec_n;
+  int eig_path = 0, eig_iters = 0;
+  double eig_res = 0.0;
   if (n <= c->D_cut) {
+    // nothing is cut (U = I); the spectrum of G_L is still recorded
     CK_CUDA(c, identity_isometry(c->U, n, st));
-    if (int r = c->eig.values(c->GL, n, c->wL, 0))
-      return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (values) failed");
-    CK_CUDA(c, spectrum_no_cut(c->wL, n, c->scal + 2, rec, spec, st));
-    pf.launched(HOTRG_ST_EIG, 2);
+    SiBatch sb{};
+    sb.P = 1;
+    sb.n = n;
+    sb.k = n;
+    sb.G[0] = c->GL;
+    sb.X[0] = c->XL;
+    sb.theta[0] = c->thL;
+    long long nl = 0;
+    CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
+    CK_CUDA(c, spectrum_no_cut(c->thL, n, 1, c->scal + 2, rec, spec, st));
+    pf.launched(HOTRG_ST_EIG, 2 + (int)nl);
     spec_n = n;
   } else {
-    const int m = Dn + 1;
-    if (int r = c->eig.top(c->GL, n, m, c->wL, 0))
-      return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (left) failed");
-    if (int r = c->eig.top(c->GR, n, m, c->wR, 1))
-      return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (right) failed");
-    SelectArgs a{n, Dn, m, c->wL, c->wR, c->GL, c->GR, c->scal + 2, c->scal + 3, c->U, rec, spec};
-    CK_CUDA(c, select_isometry(a, st));
+    // leading k = D'+1 eigenpairs of both environments (batched FP64 solver)
+    const int k = Dn + 1;
+    SiBatch sb{};
+    sb.P = 2;
+    sb.n = n;
+    sb.k = k;
+    sb.G[0] = c->GL;
+    sb.G[1] = c->GR;
+    sb.X[0] = c->XL;
+    sb.X[1] = c->XR;
+    sb.theta[0] = c->thL;
+    sb.theta[1] = c->thR;
+    long long nl = 0;
+    bool ok = false;
+    if (n + (n & 1) <= kSiMaxBlock) {
+      CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
+      eig_path = 1;
+      ok = true;
+    } else {
+      int m = ((2 * k + 7) / 8) * 8;
+      if (m > kSiMaxBlock) m = kSiMaxBlock;
+      if (m > n) m = n & ~1;
+      sb.m = m;
+      const int di = ydir ? 1 : 0;
+      if (c->nprev[di] == n && c->kprev[di] <= m) {
+        sb.warm[0] = sb.warm[1] = c->Uprev[di];
+        sb.kw = c->kprev[di];
+      }
+      SiResult r{};
+      CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, 80, st, &r, &nl));
+      eig_path = 2;
+      eig_iters = r.iterations;
+      eig_res = r.residual;
+      ok = r.converged;
+    }
+    pf.launched(HOTRG_ST_EIG, (int)nl);
+    if (ok) {
+      SelectArgs a{n, Dn, k, 1, c->thL, c->thR, c->XL, c->XR, c->scal + 2, c->scal + 3, c->U, rec, spec};
+      CK_CUDA(c, select_isometry(a, st));
+    } else {
+      // library fallback (G_L, G_R are untouched by the own solver)
+      eig_path = 3;
+      if (int r = c->eig.top(c->GL, n, k, c->wL, 0))
+        return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (left) failed");
+      if (int r = c->eig.top(c->GR, n, k, c->wR, 1))
+        return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (right) failed");
+      SelectArgs a{n, Dn, k, 0, c->wL, c->wR, c->GL, c->GR, c->scal + 2, c->scal + 3, c->U, rec, spec};
+      CK_CUDA(c, select_isometry(a, st));
+    }
     pf.launched(HOTRG_ST_EIG, 1);
-    spec_n = m;
+    const int di = ydir ? 1 : 0;
+    CK_CUDA(c, cudaMemcpyAsync(c->Uprev[di], c->U, sizeof(double) * (size_t)n * Dn,
+                               cudaMemcpyDeviceToDevice, st));
+    c->nprev[di] = n;
+    c->kprev[di] = Dn;
+    spec_n = k;
   }
   pf.end(HOTRG_ST_EIG);
   int hinfo[2] = {0, 0};
@@ -399,7 +472,7 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   CK_CUDA(c, cudaStreamSynchronize(st));
   pf.collect(false);
   if (hotrg_status fs = check_flag(c)) return fs;
-  if (hinfo[0] != 0 || (n > c->D_cut && hinfo[1] != 0))
+  if (eig_path == 3 && (hinfo[0] != 0 || hinfo[1] != 0))
     return fail(c, HOTRG_EEIG, "eigensolver info = " + std::to_string(hinfo[0]) + ", " +
                                    std::to_string(hinfo[1]));
 
@@ -461,6 +534,9 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   inf.Dx = D;
   inf.Dy = E;
   inf.Dn = Dn;
+  inf.eig_path = eig_path;
+  inf.eig_iters = eig_iters;
+  inf.eig_residual = eig_res;
   c->info.push_back(inf);
   c->spec_count.push_back(spec_n);
   return HOTRG_OK;

@@ -97,9 +97,9 @@ int TcPath::init(hotrg_prec prec, int D0, int D_cut, cudaStream_t s, int *err_fl
   I.eb = tc_elem_bytes(I.mode);
   const long long Dm = D0 > D_cut ? D0 : D_cut;
   // Per-plane capacities.  Rows are padded to a 16-byte pitch (at most 7 extra
-  // elements), so every operand fits (Dm^2 + 8)^2 elements and every D^5
-  // intermediate fits D_cut Dm^2 (Dm^2 + 8).
-  I.capT = (std::size_t)((Dm * Dm + 8) * (Dm * Dm + 8));
+  // elements): the largest operand is the a5 view of T, D E^2 rows of pitch(D)
+  // <= Dm^3 (Dm + 8) elements, and every D^5 intermediate fits D_cut Dm^2 (Dm^2 + 8).
+  I.capT = (std::size_t)(Dm * Dm * Dm * (Dm + 8));
   I.capP = (std::size_t)(D_cut * Dm * Dm * (Dm * Dm + 8));
   const std::size_t bt = I.capT * I.planes * I.eb, bp = I.capP * I.planes * I.eb;
   for (int i = 0; i < 4; ++i) {

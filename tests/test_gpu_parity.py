@@ -151,3 +151,23 @@ def test_zero_tensor_is_rejected(pkg):
     with pytest.raises(pkg.HotrgError) as e:
         pkg.Hotrg(np.zeros((2, 2, 2, 2)), 8)
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("D_cut,nsteps,paths", [(8, 10, {0, 1}), (12, 12, {0, 1, 2}), (16, 10, {0, 2})])
+def test_eigensolver_paths_and_residuals(pkg, D_cut, nsteps, paths):
+    """The own FP64 eigensolver serves every cut (no library fallback) and
+    meets its residual target; spectra agree with LAPACK's through the oracle."""
+    T0 = pkg.ising_tensor(0.44)
+    r = ref.run(ref.ising_initial_tensor(0.44), D_cut, nsteps)
+    with run_gpu(pkg, T0, D_cut, nsteps) as h:
+        seen = set()
+        for i, s in enumerate(r.steps):
+            info = h.step_info(i)
+            seen.add(info.eig_path)
+            assert info.eig_path != 3, f"step {i} fell back to the library eigensolver"
+            if info.eig_path == 2:
+                assert info.eig_residual <= 1e-12
+                assert 1 <= info.eig_iters <= 80
+        assert seen <= paths and 0 in seen
+        compare_steps(h, r, 1e-11)
+        assert abs(h.ln_z_per_site() / r.ln_z_per_site - 1) < 1e-12
