@@ -199,6 +199,31 @@ typedef struct {
 hotrg_status hotrg_profile_enable(hotrg_ctx *ctx, int enable);
 hotrg_status hotrg_profile_read(hotrg_ctx *ctx, hotrg_profile_t *out);
 
+/*
+ * Allocation-free max-norm rescale of a caller-owned device tensor (the paper
+ * has no counterpart; this is a service for callers that cannot allocate
+ * device memory: frameworks that route all device memory through their own
+ * pool and forbid other allocators, processes whose device-memory quota such a
+ * pool already holds, and latency-critical loops that cannot afford the device
+ * synchronisation cudaMalloc implies).
+ *   T       device pointer to `count` doubles, rescaled in place: T /= max|T|
+ *   count   1 <= count <= 2^26 (67,108,864); larger sizes give HOTRG_EINVAL
+ *   weight  finite factor of the log: *logsum += weight * ln(max|T|)
+ *   logsum  device pointer to one double, updated in place
+ *   stream  cudaStream_t to run on (NULL = legacy default stream)
+ * Returns HOTRG_OK, HOTRG_EINVAL, HOTRG_ECUDA, or HOTRG_ENONFINITE when max|T|
+ * is zero or not finite (T and *logsum are then left unchanged).  The call
+ * synchronises `stream` to read its status.  It allocates nothing: its scratch
+ * (1024 partial maxima and a status word, about 8 KiB) is one file-scope
+ * device array that every GPU loading the library holds until the process
+ * exits.  The first call on each device resolves that array's device address
+ * (with the device current), so make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ */
+hotrg_status hotrg_rescale_noalloc(double *T, long long count, double weight, double *logsum,
+                                   void *stream);
+
 /* Release all resources of the context; NULL is accepted and ignored. */
 void hotrg_destroy(hotrg_ctx *ctx);
 

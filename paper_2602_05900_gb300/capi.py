@@ -70,6 +70,8 @@ _SIGS = {
     "hotrg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hotrg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "hotrg_destroy": (None, [ctypes.c_void_p]),
+    "hotrg_rescale_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
