@@ -213,7 +213,9 @@ __global__ void __launch_bounds__(128, 1)
 
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * C::BM, n0 = blockIdx.y * BN;
+  // N tiles run fastest: the CTAs that share an A tile are launched together and
+  // read it from L2 instead of HBM
+  const int m0 = blockIdx.y * C::BM, n0 = blockIdx.x * BN;
   const int nkb = (K + Tr::kBK - 1) / Tr::kBK;
 
   auto a_tile = [&](int s, int p) { return smem_base + s * C::STAGE_BYTES + p * C::A_BYTES; };
@@ -297,7 +299,9 @@ __global__ void __launch_bounds__(128, 1)
   if (ok) {
     const int row = m0 + warp * 32 + lane;
     const bool rv = row < M;
-    const long long roff = rv ? map_off(epi.cm, row) : 0;
+    const long long roff = rv ? map_off(epi.cm, row) : -1;
+    // the pipeline buffers are idle now: 32 x 33 floats of staging per warp
+    float *stage = reinterpret_cast<float *>(smem_raw + (smem_base - smem_u32(smem_raw))) + warp * 32 * 33;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
       if (n0 + c * 32 >= N) break;
@@ -305,10 +309,25 @@ __global__ void __launch_bounds__(128, 1)
       tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, r);
       const int col = n0 + c * 32 + lane;
       const long long coff = (col < N) ? map_off(epi.cn, col) : -1;
+      if (!epi.transpose) {
+        // lane = row: consecutive lanes store consecutive rows (unit-stride cm)
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const long long co = __shfl_sync(0xffffffffu, coff, j);
-        if (rv && co >= 0) store_out(epi, roff + co, __uint_as_float(r[j]));
+        for (int j = 0; j < 32; ++j) {
+          const long long co = __shfl_sync(0xffffffffu, coff, j);
+          if (rv && co >= 0) store_out(epi, roff + co, __uint_as_float(r[j]));
+        }
+      } else {
+        // transpose through shared memory: lane = column of row rr
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const long long ro = __shfl_sync(0xffffffffu, roff, rr);
+          const float v = stage[rr * 33 + lane];
+          if (ro >= 0 && coff >= 0) store_out(epi, ro + coff, v);
+        }
+        __syncwarp();
       }
     }
   }
@@ -373,7 +392,7 @@ cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, i
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((M + C::BM - 1) / C::BM, (N + BN - 1) / BN);
+  dim3 grid((N + BN - 1) / BN, (M + C::BM - 1) / C::BM);
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
   k_tc_gemm<MODE, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, epi, err);
   return cudaGetLastError();
@@ -403,10 +422,13 @@ cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, 
     return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A.base) & 15) || (reinterpret_cast<uintptr_t>(B.base) & 15))
     return cudaErrorInvalidValue;
+  TcEpilogue e = epi;
+  // store layout: keep lane = row when the rows are unit-stride, else transpose
+  e.transpose = !(epi.cm.s0 == 1 && epi.cm.n0 >= 8);
   switch (mode) {
-    case TcMode::TF32: return dispatch_bn<0>(A, B, M, N, K, epi, err_flag, s);
-    case TcMode::BF16X3: return dispatch_bn<1>(A, B, M, N, K, epi, err_flag, s);
-    case TcMode::BF16X6: return dispatch_bn<2>(A, B, M, N, K, epi, err_flag, s);
+    case TcMode::TF32: return dispatch_bn<0>(A, B, M, N, K, e, err_flag, s);
+    case TcMode::BF16X3: return dispatch_bn<1>(A, B, M, N, K, e, err_flag, s);
+    case TcMode::BF16X6: return dispatch_bn<2>(A, B, M, N, K, e, err_flag, s);
   }
   return cudaErrorInvalidValue;
 }

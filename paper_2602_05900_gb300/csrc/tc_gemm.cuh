@@ -39,6 +39,8 @@ struct TcEpilogue {
   int planes;              // output planes (BF16P): 1, 2 or 3
   bool round_tf32;         // F32 output feeds a TF32 operand: round to nearest TF32
   IdxMap cm, cn;
+  bool transpose;          // set by tc_gemm: stage through shared memory so that a warp
+                           // stores 32 consecutive columns of one row (unit-stride cn)
 };
 
 // Launches one GEMM C(M x N) = A(M x K) . B(N x K)^T; returns a CUDA error
