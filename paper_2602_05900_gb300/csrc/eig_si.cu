@@ -5,10 +5,13 @@
 // two environments of a step run in the same launches), and only the small
 // m x m factorisations run on one CTA per problem.
 //
-// One iteration:  Y = G X  ->  X = orth(Y)  (shifted CholeskyQR, three passes)
-// Every few iterations a Rayleigh-Ritz step diagonalises H = X^T G X with the
-// parallel two-sided Jacobi method and rotates X, Y onto the Ritz vectors;
-// the iteration stops when ||G x_i - theta_i x_i|| <= tol * theta_0 for i < k.
+// One iteration:  Y = G X  ->  X = orth(Y): shifted CholeskyQR3 in FP64 until
+// the first Rayleigh-Ritz step, two FP32 CholeskyQR passes (FP64 rotation)
+// after it.  Before each Rayleigh-Ritz step two FP64 Newton-Schulz steps make
+// X orthonormal to FP64 accuracy; the step diagonalises H = X^T G X with the
+// parallel two-sided Jacobi method and rotates X, Y onto the Ritz vectors.  The
+// iteration stops when ||G x_i - theta_i x_i|| <= tol * theta_0 for i < k; the
+// next check is scheduled from the observed Ritz-value ratio theta_m / theta_k.
 #include <math.h>
 
 #include <algorithm>
@@ -142,31 +145,34 @@ __global__ void k_si_sum_split(Ptrs part, Ptrs out, int S, long long nm) {
 }
 
 // Cp[c] = A[rows of chunk c]^T B[same rows]   (m x m, row-major a*m + b)
-__global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int n, int m) {
-  __shared__ double As[16][kSiMaxBlock + 1];
-  __shared__ double Bs[16][kSiMaxBlock + 1];
+template <typename Acc>
+__global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int n, int m, int sym) {
+  __shared__ Acc As[16][kSiMaxBlock + 1];
+  __shared__ Acc Bs[16][kSiMaxBlock + 1];
   const int z = blockIdx.z, c = blockIdx.x;
   const double *a = A.p[z];
   const double *b = B.p[z];
   const int r0 = c * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
   const int ta = threadIdx.x >> 4, tb = threadIdx.x & 15;
   constexpr int U = kSiMaxBlock / 16;   // 6 x 6 outputs per thread
-  double acc[U][U];
+  // A^T A is symmetric: only the tiles on or above the diagonal are computed
+  const bool skip = sym && (ta > tb);
+  Acc acc[U][U];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < U; ++v) acc[u][v] = Acc(0);
   for (int rr = r0; rr < r1; rr += 16) {
     for (int e = threadIdx.x; e < 16 * m; e += 256) {
       const int j = e >> 4, ii = e & 15;
       const int row = rr + ii;
-      As[ii][j] = (row < r1) ? a[(size_t)j * n + row] : 0.0;
-      Bs[ii][j] = (row < r1) ? b[(size_t)j * n + row] : 0.0;
+      As[ii][j] = (row < r1) ? (Acc)a[(size_t)j * n + row] : Acc(0);
+      Bs[ii][j] = (row < r1) ? (Acc)b[(size_t)j * n + row] : Acc(0);
     }
     __syncthreads();
 #pragma unroll 4
-    for (int ii = 0; ii < 16; ++ii) {
-      double av[U], bv[U];
+    for (int ii = 0; ii < 16 && !skip; ++ii) {
+      Acc av[U], bv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) av[u] = As[ii][ta * U + u];
 #pragma unroll
@@ -184,25 +190,120 @@ __global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int 
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       const int ia = ta * U + u, ib = tb * U + v;
-      if (ia < m && ib < m) out[ia * m + ib] = acc[u][v];
+      if (ia < m && ib < m && !skip) out[ia * m + ib] = (double)acc[u][v];
     }
 }
 
 // C = sum over row chunks of the Gram partials (fixed order), symmetrised.
-__global__ void k_si_gram_reduce(CPtrs Cp, Ptrs C, int nchunks, int m) {
+// sym: the partials hold only the upper tiles (A^T A).  ns: write instead the
+// Newton-Schulz polish W = (3 I - C) / 2 (column-major, = row-major by symmetry).
+__global__ void k_si_gram_reduce(CPtrs Cp, Ptrs C, int nchunks, int m, int sym, int ns) {
   const int z = blockIdx.z;
   const long long mm = (long long)m * m;
+  constexpr int U = kSiMaxBlock / 16;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int a = e / m, b = e % m;
     if (b < a) continue;
-    double v = 0.0, w = 0.0;
-    for (int c = 0; c < nchunks; ++c) {
-      v += Cp.p[z][c * mm + a * m + b];
-      w += Cp.p[z][c * mm + b * m + a];
+    const double *src = Cp.p[z];
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    double sv;
+    if (sym) {
+      // (a, b) lives in tile (a / U, b / U); a tile below the diagonal was skipped
+      const bool upper = (a / U) <= (b / U);
+      const long long off = upper ? (long long)a * m + b : (long long)b * m + a;
+      int c = 0;
+      for (; c + 4 <= nchunks; c += 4) {
+        v0 += src[c * mm + off];
+        v1 += src[(c + 1) * mm + off];
+        v2 += src[(c + 2) * mm + off];
+        v3 += src[(c + 3) * mm + off];
+      }
+      for (; c < nchunks; ++c) v0 += src[c * mm + off];
+      sv = (v0 + v1) + (v2 + v3);
+    } else {
+      double w0 = 0.0, w1 = 0.0;
+      int c = 0;
+      for (; c + 2 <= nchunks; c += 2) {
+        v0 += src[c * mm + a * m + b];
+        w0 += src[c * mm + b * m + a];
+        v1 += src[(c + 1) * mm + a * m + b];
+        w1 += src[(c + 1) * mm + b * m + a];
+      }
+      for (; c < nchunks; ++c) {
+        v0 += src[c * mm + a * m + b];
+        w0 += src[c * mm + b * m + a];
+      }
+      sv = 0.5 * ((v0 + v1) + (w0 + w1));
     }
-    const double sv = 0.5 * (v + w);
+    if (ns) sv = (a == b ? 1.5 : 0.0) - 0.5 * sv;
     C.p[z][a * m + b] = sv;
     C.p[z][b * m + a] = sv;
+  }
+}
+
+// Shifted, column-scaled Cholesky in FP32 of a block's Gram matrix C and the
+// rotation W = diag(d) R^-1 (column-major, stored in FP64) such that Y W is
+// orthonormal up to FP32 accuracy: C_hat = diag(d) C diag(d) + shift I = R^T R,
+// d_j = 1 / sqrt(C_jj).  Used for the iterations between Rayleigh-Ritz steps,
+// where an approximately orthonormal basis is all the power iteration needs.
+__global__ void __launch_bounds__(kCholThreads) k_si_chol32(CPtrs Cin, int m, float shift, Ptrs Wout,
+                                                            int *flag) {
+  extern __shared__ float shf[];
+  const int ld = m + 1;
+  float *C = shf;                 // m x ld, upper triangle -> R
+  float *Z = shf + m * ld;        // m x ld, R^-1 (upper)
+  float *d = Z + m * ld;          // m
+  float *rinv = d + m;            // m
+  const int z = blockIdx.z;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double cjj = Cin.p[z][(size_t)j * m + j];
+    d[j] = (cjj > 0.0 && isfinite(cjj)) ? (float)rsqrt_fp64(cjj) : 1.0f;
+  }
+  __syncthreads();
+  for (int a = ty; a < m; a += 16)
+    for (int b = tx; b < m; b += 16)
+      C[a * ld + b] = (float)Cin.p[z][(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? shift : 0.0f);
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const float piv = C[j * ld + j];
+    if (!(piv > 0.0f) || !isfinite(piv)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;
+    }
+    const float ri = rsqrtf(piv);
+    __syncthreads();
+    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) C[j * ld + l] *= ri;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      C[j * ld + j] = piv * ri;
+      rinv[j] = ri;
+    }
+    for (int a = j + 1 + ty; a < m; a += 16)
+      for (int b = a + tx; b < m; b += 16) C[a * ld + b] = fmaf(-C[j * ld + a], C[j * ld + b], C[a * ld + b]);
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(flag, 1);
+    return;
+  }
+  for (int a = ty; a < m; a += 16)
+    for (int b = tx; b < m; b += 16) Z[a * ld + b] = (a == b) ? 1.0f : 0.0f;
+  __syncthreads();
+  for (int i = m - 1; i >= 0; --i) {
+    for (int b = i + threadIdx.x; b < m; b += blockDim.x) Z[i * ld + b] *= rinv[i];
+    __syncthreads();
+    for (int a = ty; a < i; a += 16)
+      for (int b = i + tx; b < m; b += 16) Z[a * ld + b] = fmaf(-C[a * ld + i], Z[i * ld + b], Z[a * ld + b]);
+    __syncthreads();
+  }
+  double *W = Wout.p[z];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int c = e / m, j = e % m;           // W[j + c m]
+    W[e] = (j <= c) ? (double)Z[j * ld + c] * (double)d[j] : 0.0;
   }
 }
 
@@ -497,7 +598,8 @@ __global__ void __launch_bounds__(512) k_si_jacobi(CPtrs Cin, int m, Ptrs Wout, 
 }
 
 // Out = A . W  (A, Out n x m column-major; W m x m column-major: W[j + c m])
-__global__ void __launch_bounds__(256) k_si_rotate(CPtrs A, CPtrs W, Ptrs Out, int n, int m) {
+// tri: W is upper triangular (W[j, c] = 0 for j > c), so j-blocks past the tile's last column are skipped
+__global__ void __launch_bounds__(256) k_si_rotate(CPtrs A, CPtrs W, Ptrs Out, int n, int m, int tri) {
   __shared__ double As[32][33];
   __shared__ double Ws[32][33];
   const int z = blockIdx.z;
@@ -506,7 +608,8 @@ __global__ void __launch_bounds__(256) k_si_rotate(CPtrs A, CPtrs W, Ptrs Out, i
   const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int j0 = 0; j0 < m; j0 += 32) {
+  const int jend = tri ? min(m, c0 + 32) : m;
+  for (int j0 = 0; j0 < jend; j0 += 32) {
     for (int e = threadIdx.x; e < 32 * 32; e += 256) {
       const int jj = e >> 5, ii = e & 31;
       const int row = i0 + ii, j = j0 + jj;
@@ -639,6 +742,7 @@ size_t jacobi_smem(int m) {
          (size_t)(2 * half + 2) * sizeof(int) + 64;
 }
 size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
+size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(float); }
 
 cudaError_t set_attrs() {
   static bool done = false;
@@ -646,7 +750,8 @@ cudaError_t set_attrs() {
   cudaError_t e;
   const int big = 200 * 1024;
   if ((e = cudaFuncSetAttribute(k_si_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
-      (e = cudaFuncSetAttribute(k_si_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+      (e = cudaFuncSetAttribute(k_si_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
+      (e = cudaFuncSetAttribute(k_si_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   done = true;
   return cudaSuccess;
@@ -729,30 +834,61 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       nl += 2;
     }
   };
-  // C = A^T B (m x m), symmetrised
-  auto gram = [&](double *const *A, double *const *Bm) {
-    k_si_gram<<<dim3(L.NC, 1, P), 256, 0, s>>>(cp_of(A, P), cp_of(Bm, P), p_of(B.Cp, P), n, m);
-    k_si_gram_reduce<<<dim3(grid_1d(L.mm), 1, P), 256, 0, s>>>(cp_of(B.Cp, P), p_of(B.C, P), L.NC, m);
+  // C = A^T B (m x m), symmetrised; ns: write the Newton-Schulz polish (3I - C)/2 instead
+  auto gram = [&](double *const *A, double *const *Bm, bool sym, bool f32, bool ns) {
+    if (f32)
+      k_si_gram<float><<<dim3(L.NC, 1, P), 256, 0, s>>>(cp_of(A, P), cp_of(Bm, P), p_of(B.Cp, P), n, m, sym);
+    else
+      k_si_gram<double><<<dim3(L.NC, 1, P), 256, 0, s>>>(cp_of(A, P), cp_of(Bm, P), p_of(B.Cp, P), n, m, sym);
+    k_si_gram_reduce<<<dim3(grid_1d(L.mm), 1, P), 256, 0, s>>>(cp_of(B.Cp, P), p_of(B.C, P), L.NC, m, sym, ns);
     nl += 2;
   };
-  // one CholeskyQR pass: dst = src diag(1/d) R^-1
-  auto cholqr = [&](double *const *src, double *const *dst, double sh) {
-    gram(src, src);
+  // one CholeskyQR pass in FP32 (Gram and factor), rotation in FP64: dst = src W
+  auto cholqr32 = [&](double *const *src, double *const *dst, float sh) {
+    gram(src, src, true, true, false);
+    k_si_chol32<<<gz, kCholThreads, chol32_smem(m), s>>>(cp_of(B.C, P), m, sh, p_of(B.W, P), B.flag);
+    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.W, P), p_of(dst, P), n, m, 1);
+    nl += 2;
+  };
+  // one CholeskyQR pass in FP64 (robust for any conditioning with the shift)
+  auto cholqr64 = [&](double *const *src, double *const *dst, double sh) {
+    gram(src, src, true, false, false);
     k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(cp_of(B.C, P), m, sh, p_of(B.W, P), B.flag);
-    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.W, P), p_of(dst, P), n, m);
+    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.W, P), p_of(dst, P), n, m, 1);
     nl += 2;
   };
-  // dst = orth(src) by shifted CholeskyQR3: src -> tmp -> src -> dst
-  auto orth = [&](double **src, double **tmp, double **dst) {
-    cholqr(src, tmp, shift);
-    cholqr(tmp, src, 0.0);
-    cholqr(src, dst, 0.0);
+  // FP64 Newton-Schulz step towards orthonormality: dst = src (3I - src^T src) / 2
+  auto polish = [&](double *const *src, double *const *dst) {
+    gram(src, src, true, false, true);
+    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.C, P), p_of(dst, P), n, m, 0);
+    nl += 1;
+  };
+  // dst = orth(src) through tmp (src is overwritten).  Until the first
+  // Rayleigh-Ritz step the power-iterated block can be arbitrarily ill
+  // conditioned: shifted CholeskyQR3 in FP64.  Afterwards the basis holds Ritz
+  // vectors, G X is X Theta up to the residual, its column-scaled Gram matrix is
+  // close to I, and two FP32 CholeskyQR passes suffice for the power iteration.
+  auto orth = [&](double **src, double **tmp, double **dst, bool after_rr) {
+    if (after_rr) {
+      cholqr32(src, tmp, 0.0f);
+      cholqr32(tmp, dst, 0.0f);
+    } else {
+      cholqr64(src, tmp, shift);
+      cholqr64(tmp, src, 0.0);
+      cholqr64(src, dst, 0.0);
+    }
+  };
+  // x = FP64-orthonormal x (two Newton-Schulz steps through tmp)
+  auto polish2 = [&](double **x, double **tmp) {
+    polish(x, tmp);
+    polish(tmp, x);
   };
 
   if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
   k_si_init<<<dim3(grid_1d(L.nm), 1, P), 256, 0, s>>>(p_of(X, P), cp_of(b.warm, P), b.kw, n, m);
   nl += 1;
-  orth(X, Z, Y);                    // orthonormal start in Y
+  cholqr32(X, Z, 0.0f);             // a random start is well conditioned
+  cholqr32(Z, Y, 0.0f);
   for (int p = 0; p < P; ++p) std::swap(X[p], Y[p]);
 
   res->converged = false;
@@ -762,15 +898,17 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   int next_check = 3;
   std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
   while (it < max_iter) {
+    const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
+    if (check) polish2(X, Z);       // the Rayleigh-Ritz step needs an FP64-orthonormal basis
     gemm(X, Y);                     // Y = G X
     ++it;
-    if (it >= next_check || it == max_iter) {
-      gram(X, Y);                   // H = X^T G X
+    if (check) {
+      gram(X, Y, false, false, false);   // H = X^T G X
       if ((e = launch_jacobi(cp_of(B.C, P), m, p_of(B.W, P), p_of(b.theta, P), B.flag, B.sweeps, P, s)))
         return e;
-      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(X, P), cp_of(B.W, P), p_of(Z, P), n, m);
+      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(X, P), cp_of(B.W, P), p_of(Z, P), n, m, 0);
       for (int p = 0; p < P; ++p) std::swap(X[p], Z[p]);
-      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(Y, P), cp_of(B.W, P), p_of(Z, P), n, m);
+      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(Y, P), cp_of(B.W, P), p_of(Z, P), n, m, 0);
       for (int p = 0; p < P; ++p) std::swap(Y[p], Z[p]);
       k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(cp_of(X, P), cp_of(Y, P), cp_of(b.theta, P), p_of(B.res, P), n, k);
       nl += 4;
@@ -806,7 +944,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
         need = (int)std::ceil(std::log(tol / worst) / std::log(rho)) + 1;
       next_check = it + std::max(1, std::min(need, 8));
     }
-    orth(Y, Z, X);                  // X = orth(G X)
+    orth(Y, Z, X, res->rr > 0);     // X = orth(G X)
   }
   res->iterations = it;
   // the Ritz vectors must end in the caller's X buffers
