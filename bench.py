@@ -74,6 +74,26 @@ def peaks():
     return 1900.0, 1700.0, 6800.0, "fallback"
 
 
+def captured_traffic(workload, precision):
+    """DRAM bytes per a6 launch from a committed ncu summary, or None when the
+    summary is for another workload or the GEMM kernel source changed since."""
+    import hashlib
+    import glob
+    src = os.path.join(ROOT, "paper_2602_05900_gb300", "csrc", "tc_gemm.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "a6_*.md")):
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.startswith("    "):
+                k, v = line.strip().split(":", 1)
+                fields[k.strip()] = v.strip()
+        if (fields.get("kernel-source-sha256") == sha
+                and fields.get("workload") == f"{workload} {precision}"
+                and "traffic-bytes-per-launch" in fields):
+            return int(fields["traffic-bytes-per-launch"])
+    return None
+
+
 def golden(name):
     path = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
     if os.path.exists(path):
@@ -227,7 +247,9 @@ def run_ours(args, world, rank, local):
     roofline = {"kernel": "k_tc_gemm a6 bond contraction Q=P.T" if prec != "fp64" else "k_gemm_f64 a6",
                 "bound": "tensor" if prec != "fp64" else "alu", "achieved": round(achieved, 2),
                 "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_source": peak_note,
+                "traffic": captured_traffic(cfg.name, prec), "traffic_unit": "bytes/launch",
+                "algorithmic_bytes": 4 * (D ** 5 + D ** 4 + D ** 5) if prec == "tf32" else None,
+                "peak_source": peak_note,
                 "flops_per_launch": q_flops, "ms_per_launch": round(q_ms, 5)}
 
     out = {"metric": METRIC, "value": round(value, 4), "unit": "RG-steps/s", "n_gpus": world,

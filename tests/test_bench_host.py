@@ -1,0 +1,65 @@
+"""CPU checks of bench.py's host logic: the multi-rank max reduction over gloo
+(world size 2), the algorithmic flop count, the traffic lookup, and the
+reference arm's JSON line (the FP64 oracle on the host cores)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    v = bench.reduce_max(float(rank + 1) * 1.5, world)
+    bench.barrier(world)
+    out[rank] = v
+    dist.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert dict(out) == {0: 3.0, 1: 3.0}
+
+
+def test_single_rank_reduce_is_identity():
+    assert bench.reduce_max(2.5, 1) == 2.5
+
+
+def test_step_flops():
+    D = 32
+    assert bench.step_flops(D, D, D) == 2 * D ** 7 + 16 * D ** 6
+
+
+def test_captured_traffic_only_for_profiled_workload():
+    v = bench.captured_traffic("ising_044_d32", "tf32")
+    assert v is None or v > 4 * 32 ** 5              # at least the read of P (part of Q stays in L2)
+    assert bench.captured_traffic("potts3_d64", "bf16x3") is None
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "ising_bc_d8", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "RG-steps/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0

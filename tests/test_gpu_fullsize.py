@@ -1,0 +1,125 @@
+"""GPU parity at the benchmark sizes (D_cut = 32 and 48).
+
+* Whole jobs against stored FP64-oracle values (`tests/golden/oracle_values.json`,
+  written by `tests/golden/make_oracle_values.py`, which calls only `oracle/`).
+* One full-size step checked element by element: the GPU's own input tensor and
+  isometry are read back, the oracle rebuilds both environments from the input and
+  single output elements from their definitions (`oracle.sampled`), and the GPU's
+  U is checked to be an orthonormal set of eigenvectors of the chosen environment.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hotrg as ref
+from oracle import sampled
+from workloads import CONFIGS
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_values.json")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_05900_gb300 as p
+    p.load()
+    return p
+
+
+def golden(name):
+    data = json.load(open(GOLDEN))
+    if name not in data:
+        pytest.skip(f"no stored oracle value for {name}")
+    return data[name]
+
+
+def initial(pkg, cfg):
+    return pkg.ising_tensor(cfg.beta, cfg.h) if cfg.family == "ising" else pkg.potts_tensor(cfg.q, cfg.beta)
+
+
+@pytest.mark.parametrize("name", ["ising_bc_d8", "ising_044_d32", "ising_044h_d48"])
+def test_fp64_full_job_vs_stored_oracle(pkg, name):
+    cfg, g = CONFIGS[name], golden(name)
+    with pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, "fp64") as h:
+        h.run(cfg.steps)
+        lz = h.ln_z_per_site()
+        for i, s in enumerate(g["per_step"]):
+            info = h.step_info(i)
+            assert (info.Dx, info.Dy, info.Dn) == (s["Dx"], s["Dy"], s["Dn"])
+            assert abs(info.trace_G / s["trace_G"] - 1) < 1e-10
+    assert abs(lz / g["ln_z_per_site"] - 1) < 1e-12
+
+
+@pytest.mark.parametrize("name,prec,tol", [("ising_044_d32", "tf32", 5e-4), ("ising_044h_d48", "bf16x3", 2e-5),
+                                           ("ising_044h_d48", "bf16x6", 2e-6)])
+def test_mixed_full_job_error_vs_stored_oracle(pkg, name, prec, tol):
+    cfg, g = CONFIGS[name], golden(name)
+    with pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, prec) as h:
+        h.run(cfg.steps)
+        err = abs(h.ln_z_per_site() / g["ln_z_per_site"] - 1)
+    print(f"{name} {prec}: relative ln Z/N error vs FP64 oracle = {err:.3e}")
+    assert err < tol
+
+
+def run_to_steady(pkg, cfg, prec):
+    h = pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, prec)
+    d = "x"
+    while True:
+        dx, dy, _ = h.dims()
+        if dx == cfg.D_cut and dy == cfg.D_cut:
+            return h, d
+        h.step(d)
+        d = "y" if d == "x" else "x"
+
+
+@pytest.mark.parametrize("name,prec", [("ising_044h_d48", "fp64"), ("ising_044_d32", "fp64"),
+                                       ("ising_044h_d48", "tf32")])
+def test_sampled_full_size_step(pkg, name, prec):
+    cfg = CONFIGS[name]
+    h, d = run_to_steady(pkg, cfg, prec)
+    with h:
+        T_in = h.tensor()                                   # normalised input of the step
+        h.step(d)
+        i = h.dims()[2] - 1
+        info = h.step_info(i)
+        U = h.isometry()
+        T_out = h.tensor()
+        spec = h.spectrum(i)
+    view = np.ascontiguousarray(T_in.transpose(2, 3, 0, 1)) if d == "x" else T_in
+    D = view.shape[0]
+    n, Dn = D * D, info.Dn
+    assert U.shape == (n, Dn)
+    tol_u = 1e-12 if prec == "fp64" else 1e-10
+    assert np.abs(U.T @ U - np.eye(Dn)).max() < tol_u
+
+    # the chosen environment, from its definition-level regrouping in FP64
+    G_L, G_R = ref.gram_environments(view)
+    G = G_L if info.side == 0 else G_R
+    lam = np.linalg.eigvalsh(G)[::-1]
+    GU = G @ U
+    ritz = np.einsum("ia,ia->a", U, GU)
+    resid = np.abs(GU - U * ritz).max() / lam[0]
+    tol_eig = 1e-10 if prec == "fp64" else 5e-3
+    assert resid < tol_eig, resid
+    # the kept values are the leading ones; the spectrum matches LAPACK's
+    tol_spec = 1e-11 if prec == "fp64" else 5e-3
+    assert np.allclose(spec[:Dn], lam[:Dn] / lam[0], rtol=0, atol=tol_spec)
+    assert abs(info.trace_G / np.trace(G_L) - 1) < (1e-12 if prec == "fp64" else 1e-3)
+
+    # sampled output elements T'[a,b,y,y'] (before the rescale) from their definition
+    rng = np.random.default_rng(7)
+    E = view.shape[2]
+    samples = [tuple(int(v) for v in rng.integers(0, [Dn, Dn, E, E])) for _ in range(48)]
+    ref_vals = sampled.projected_elements(view, U, samples)
+    c = np.exp(info.ln_c)
+    out = np.ascontiguousarray(T_out.transpose(2, 3, 0, 1)) if d == "x" else T_out
+    got = np.array([out[s] for s in samples]) * c
+    scale = c                                           # max |T'| before the rescale
+    tol_t = 1e-12 if prec == "fp64" else 2e-3
+    assert np.abs(got - ref_vals).max() < tol_t * scale
