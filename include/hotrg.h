@@ -33,9 +33,9 @@
  *     the first error seen by a context is latched: later calls on it return
  *     the same status without doing work, and hotrg_last_error() returns a
  *     message.  A NULL context pointer gives HOTRG_EINVAL.
- *   - hotrg_step enqueues work on the context's stream.  It synchronises that
- *     stream once per step (the eigensolver reports its result count to the
- *     host); device-side faults surface at the next synchronising call.
+ *   - hotrg_step enqueues work on the context's stream and synchronises that
+ *     stream during the step (the eigensolver's convergence checks) and once
+ *     at its end, where device-side errors of the step are reported.
  *   - A context may be used by one host thread at a time.
  */
 #ifndef HOTRG_H
@@ -223,6 +223,39 @@ hotrg_status hotrg_profile_read(hotrg_ctx *ctx, hotrg_profile_t *out);
  */
 hotrg_status hotrg_rescale_noalloc(double *T, long long count, double weight, double *logsum,
                                    void *stream);
+
+/*
+ * Batches (many independent lattice models in one context).  Every instance
+ * is its own HOTRG run with its own T0 and D_cut; all instances take the same
+ * step directions.  Instances with equal (D0, D_cut) have equal bond
+ * dimensions after every step and are grouped: each kernel of a step runs once
+ * per group over all its instances, and the eigensolver diagonalises the
+ * group's 2G environments as one batch.  Results of an instance do not depend
+ * on which other instances share its context.
+ *
+ * hotrg_batch_create: n instances (1 <= n <= 4096); T0s[i] is a host pointer
+ *   to D0s[i]^4 doubles ([x,x',y,y'] row-major, borrowed and copied),
+ *   1 <= D0s[i] <= 64 and 1 <= Dcuts[i] <= 64.  prec, stream, ownership and
+ *   errors as for hotrg_create (all device memory is allocated here).
+ * hotrg_batch_step: one step of every instance (same as hotrg_step).
+ * hotrg_batch_size: number of instances.
+ * hotrg_batch_log_z: ln Z / N of every instance, in creation order, into
+ *   out_n[0..n) (host, n doubles; synchronises).
+ * hotrg_batch_step_info / hotrg_batch_get_tensor: hotrg_step_info and
+ *   hotrg_get_tensor for instance `inst` (0-based, creation order).
+ * On a context with more than one instance, hotrg_log_z_per_site and
+ * hotrg_free_energy return HOTRG_ESTATE; hotrg_step_info, hotrg_spectrum,
+ * hotrg_get_tensor, hotrg_get_isometry and hotrg_dims report instance 0.
+ */
+hotrg_status hotrg_batch_create(int n, const double *const *T0s, const int *D0s,
+                                const int *Dcuts, hotrg_prec prec, void *stream,
+                                hotrg_ctx **out);
+hotrg_status hotrg_batch_step(hotrg_ctx *ctx, hotrg_dir dir);
+hotrg_status hotrg_batch_size(hotrg_ctx *ctx, int *n);
+hotrg_status hotrg_batch_log_z(hotrg_ctx *ctx, double *out_n);
+hotrg_status hotrg_batch_step_info(hotrg_ctx *ctx, int inst, int step, hotrg_step_info_t *out);
+hotrg_status hotrg_batch_get_tensor(hotrg_ctx *ctx, int inst, double *host_out, long long cap,
+                                    int dims[4]);
 
 /* Release all resources of the context; NULL is accepted and ignored. */
 void hotrg_destroy(hotrg_ctx *ctx);

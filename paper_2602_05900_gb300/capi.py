@@ -69,6 +69,15 @@ _SIGS = {
     "hotrg_dims": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip]),
     "hotrg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hotrg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
+    "hotrg_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_dp), _ip, _ip, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "hotrg_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hotrg_batch_size": (ctypes.c_int, [ctypes.c_void_p, _ip]),
+    "hotrg_batch_log_z": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "hotrg_batch_step_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(StepInfo)]),
+    "hotrg_batch_get_tensor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_longlong,
+                                              _ip]),
     "hotrg_destroy": (None, [ctypes.c_void_p]),
     "hotrg_rescale_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p]),
@@ -105,6 +114,11 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
+def _stream_handle(stream):
+    return ctypes.c_void_p(stream if isinstance(stream, int) else
+                           (stream.cuda_stream if stream is not None else 0))
+
+
 def ising_tensor(beta: float, h: float = 0.0) -> np.ndarray:
     out = np.zeros((2, 2, 2, 2))
     s = load().hotrg_ising_tensor(beta, h, _ptr(out))
@@ -131,10 +145,8 @@ class Hotrg:
         if T0.shape != (D0, D0, D0, D0):
             raise ValueError("T0 must have shape (D0, D0, D0, D0)")
         handle = ctypes.c_void_p()
-        st = ctypes.c_void_p(stream if isinstance(stream, int) else
-                             (stream.cuda_stream if stream is not None else 0))
-        s = lib.hotrg_create(_ptr(T0), D0, int(D_cut), PRECISIONS[precision], st,
-                             ctypes.byref(handle))
+        s = lib.hotrg_create(_ptr(T0), D0, int(D_cut), PRECISIONS[precision],
+                             _stream_handle(stream), ctypes.byref(handle))
         if s:
             raise HotrgError(s, f"hotrg_create failed: {status_string(s)}")
         self._h = handle
@@ -224,3 +236,71 @@ class Hotrg:
 
     def __exit__(self, *a):
         self.close()
+
+
+class HotrgBatch:
+    """Many independent HOTRG instances in one context (``hotrg_batch_*``).
+
+    ``T0s`` is a sequence of initial tensors (each (D0, D0, D0, D0)) and
+    ``D_cuts`` the matching cuts; all instances take the same step directions.
+    """
+
+    def __init__(self, T0s, D_cuts, precision: str = "tf32", stream=None):
+        lib = load()
+        self._T0s = [np.ascontiguousarray(t, dtype=np.float64) for t in T0s]
+        n = len(self._T0s)
+        if n == 0 or len(D_cuts) != n:
+            raise ValueError("need one D_cut per initial tensor")
+        for t in self._T0s:
+            if t.ndim != 4 or len(set(t.shape)) != 1:
+                raise ValueError("every T0 must have shape (D0, D0, D0, D0)")
+        ptrs = (_dp * n)(*[_ptr(t) for t in self._T0s])
+        d0 = (ctypes.c_int * n)(*[t.shape[0] for t in self._T0s])
+        dc = (ctypes.c_int * n)(*[int(d) for d in D_cuts])
+        handle = ctypes.c_void_p()
+        s = lib.hotrg_batch_create(n, ptrs, d0, dc, PRECISIONS[precision], _stream_handle(stream),
+                                   ctypes.byref(handle))
+        if s:
+            raise HotrgError(s, f"hotrg_batch_create failed: {status_string(s)}")
+        self._h = handle
+        self.n = n
+        self.D_cuts = [int(d) for d in D_cuts]
+        self.precision = precision
+
+    _check = Hotrg._check
+    close = Hotrg.close
+    __del__ = Hotrg.__del__
+    __enter__ = Hotrg.__enter__
+    __exit__ = Hotrg.__exit__
+    profile_enable = Hotrg.profile_enable
+    profile_read = Hotrg.profile_read
+
+    def step(self, direction: str):
+        self._check(load().hotrg_batch_step(self._h, DIR_X if direction == "x" else DIR_Y),
+                    "hotrg_batch_step")
+
+    run = Hotrg.run
+
+    def size(self) -> int:
+        n = ctypes.c_int()
+        self._check(load().hotrg_batch_size(self._h, ctypes.byref(n)), "hotrg_batch_size")
+        return n.value
+
+    def ln_z_per_site(self) -> np.ndarray:
+        out = np.zeros(self.n)
+        self._check(load().hotrg_batch_log_z(self._h, _ptr(out)), "hotrg_batch_log_z")
+        return out
+
+    def step_info(self, inst: int, step: int) -> StepInfo:
+        out = StepInfo()
+        self._check(load().hotrg_batch_step_info(self._h, inst, step, ctypes.byref(out)),
+                    "hotrg_batch_step_info")
+        return out
+
+    def tensor(self, inst: int) -> np.ndarray:
+        dims = (ctypes.c_int * 4)()
+        load().hotrg_batch_get_tensor(self._h, inst, None, 0, dims)
+        out = np.zeros((dims[0], dims[1], dims[2], dims[3]))
+        self._check(load().hotrg_batch_get_tensor(self._h, inst, _ptr(out), out.size, dims),
+                    "hotrg_batch_get_tensor")
+        return out

@@ -1,4 +1,7 @@
 // Shared declarations of libhotrg's CUDA sources.
+//
+// Every kernel works on a uniform batch of instances (same shapes, buffers at a
+// fixed per-instance stride); a single HOTRG instance is a batch of one.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,6 +35,23 @@ __host__ __device__ inline long long map_off(const IdxMap &m, long long i) {
   return i0 * m.s0 + i1 * m.s1 + i2 * m.s2;
 }
 
+// A family of buffers indexed by problem z: even z -> b0, odd z -> b1, plus
+// (z / 2) * stride.  The two environments of instance i are problems 2i (left)
+// and 2i + 1 (right); pset_linear(base, s) is simply "problem z at base + z s".
+struct PSet {
+  double *b0, *b1;
+  long long stride;
+  __host__ __device__ double *at(int z) const {
+    return ((z & 1) ? b1 : b0) + (long long)(z >> 1) * stride;
+  }
+};
+inline PSet pset_pairs(double *left, double *right, long long inst_stride) {
+  return PSet{left, right, inst_stride};
+}
+inline PSet pset_linear(double *base, long long stride) {
+  return PSet{base, base + stride, 2 * stride};
+}
+
 // Stage boundaries and launch counts reported to the context's profiler.
 struct StageHook {
   virtual void begin(int stage) = 0;
@@ -40,7 +60,8 @@ struct StageHook {
   virtual ~StageHook() {}
 };
 
-// C(m, n) = sum_k A(m, k) * B(n, k) over mapped operands.
+// C(m, n) = sum_k A(m, k) * B(n, k) over mapped operands, for `batch`
+// instances whose operands lie bA, bB, bC elements apart.
 struct MappedGemm {
   int M, N, K;
   const double *A;
@@ -49,36 +70,48 @@ struct MappedGemm {
   IdxMap bn, bk;
   double *C;
   IdxMap cm, cn;
+  int batch;
+  long long bA, bB, bC;
 };
 
 // gemm_f64.cu
 cudaError_t gemm_f64(const MappedGemm &g, cudaStream_t s);
 
-// elementwise.cu
-cudaError_t symmetrize_trace(double *G, int n, double *trace_out, cudaStream_t s);
-cudaError_t identity_isometry(double *U, int n, cudaStream_t s);
-cudaError_t maxabs_scale_log(double *T, long long count, double *scratch_max, double *logsum,
-                             double inv_two_pow_n, double *ln_c_out, int *err_flag, cudaStream_t s);
-cudaError_t periodic_trace(const double *T, int Dx, int Dy, double *out, cudaStream_t s);
-cudaError_t scale_initial(double *T, long long count, double *scratch_max, double *logsum,
-                          int *err_flag, cudaStream_t s);
+// elementwise.cu  (all batched over `batch` instances with the given strides)
+cudaError_t symmetrize_trace(double *G, int n, long long sG, double *trace_out, long long sTr,
+                             int batch, cudaStream_t s);
+cudaError_t identity_isometry(double *U, int n, long long sU, int batch, cudaStream_t s);
+// T /= max|T| per instance, logsum += ln(max) * inv_two_pow_n, ln_c_out (may be null)
+// receives ln(max); scratch holds one word per instance (stride sScratch doubles).
+cudaError_t maxabs_scale_log(double *T, long long count, long long sT, double *scratch,
+                             long long sScratch, double *logsum, long long sLog,
+                             double inv_two_pow_n, double *ln_c_out, long long sLnc, int *err_flag,
+                             int batch, cudaStream_t s);
+cudaError_t periodic_trace(const double *T, int Dx, int Dy, long long sT, double *out,
+                           long long sOut, int batch, cudaStream_t s);
 
-// Device-side choice of the environment side and assembly of U (descending
-// eigenvectors, sign-fixed) plus the step record.  eig_L / eig_R hold `m`
-// ascending eigenpairs (values wL/wR, column-major vectors with leading dim n)
-// of the top of each spectrum.
+// Device-side choice of the environment side and assembly of U (sign-fixed
+// leading eigenvectors) plus the step record, for every instance i: its left
+// environment is eigen-problem 2i, its right one 2i + 1.
 struct SelectArgs {
-  int n, Dn, m;               // matrix size, kept count, eigenpairs computed per side
+  int n, Dn, m;               // matrix size, kept count, eigenpairs available per side
   int desc;                   // 1: values/vectors in descending order, 0: ascending
-  const double *wL, *wR;      // eigenvalues (m)
-  const double *vL, *vR;      // eigenvectors, column-major n x m
-  const double *trL, *trR;    // traces of G_L, G_R
-  double *U;                  // out: n x Dn column-major
-  double *record;             // out: [side, eps_L, eps_R, cut_gap, trace_G]
-  double *spectrum;           // out: normalised spectrum, Dn (+1 if cut) values
+  PSet w;                     // eigenvalues of problem z: w.at(z)[0..m)
+  PSet v;                     // eigenvectors of problem z: column-major n x m at v.at(z)
+  const double *tr;           // traces: tr + i * sTr + {0: G_L, 1: G_R}
+  long long sTr;
+  double *U;                  // out: U + i * sU, n x Dn column-major
+  long long sU;
+  double *record;             // out: record + i * sRec: [side, eps_L, eps_R, cut_gap, trace_G]
+  long long sRec;
+  double *spectrum;           // out: spectrum + i * sSpec
+  long long sSpec;
+  int batch;
 };
 cudaError_t select_isometry(const SelectArgs &a, cudaStream_t s);
-cudaError_t spectrum_no_cut(const double *w, int n, int desc, const double *trL, double *record,
-                            double *spectrum, cudaStream_t s);
+// no cut: record + spectrum of the left environment only (eigen-problem i of w)
+cudaError_t spectrum_no_cut(PSet w, int n, int desc, const double *tr, long long sTr,
+                            double *record, long long sRec, double *spectrum, long long sSpec,
+                            int batch, cudaStream_t s);
 
 }  // namespace hotrg

@@ -33,8 +33,6 @@ constexpr int kCluster = 8;      // CTAs per Jacobi problem (one thread-block cl
 constexpr int kJacobiMaxSweeps = 40;
 constexpr int kCholThreads = 256;
 
-struct Ptrs { double *p[kSiMaxBatch]; };
-struct CPtrs { const double *p[kSiMaxBatch]; };
 
 // splitmix64 finaliser (Steele, Lea, Flood 2014) -> uniform double in [-1, 1)
 __device__ inline double hash_uniform(unsigned long long x) {
@@ -73,27 +71,27 @@ __device__ inline double rsqrt_fp64(double x) {
   return y * root_s;
 }
 
-__global__ void k_si_init(Ptrs X, CPtrs warm, int kw, int n, int m) {
+__global__ void k_si_init(PSet X, PSet warm, int has_warm, int kw, int n, int m) {
   const int z = blockIdx.z;
   const long long total = (long long)n * m;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e / n);
     double v;
-    if (warm.p[z] && j < kw) v = warm.p[z][e];
+    if (has_warm && j < kw) v = warm.at(z)[e];
     else v = hash_uniform(((unsigned long long)z << 56) ^ ((unsigned long long)j << 32) ^ (unsigned long long)(e % n));
-    X.p[z][e] = v;
+    X.at(z)[e] = v;
   }
 }
 
 // Out_s = G[rows i0.., cols in split s] . X[those rows, :]  (X, Out column-major n x m)
-__global__ void __launch_bounds__(256) k_si_gemm(CPtrs G, CPtrs X, Ptrs Out, int n, int m, int chunk) {
+__global__ void __launch_bounds__(256) k_si_gemm(PSet G, PSet X, PSet Out, int n, int m, int chunk) {
   __shared__ double Gs[16][65];
   __shared__ double Xs[16][kSiMaxBlock];
   const int z = blockIdx.z;
-  const double *g = G.p[z];
-  const double *x = X.p[z];
-  double *out = Out.p[z] + (size_t)blockIdx.y * n * m;
+  const double *g = G.at(z);
+  const double *x = X.at(z);
+  double *out = Out.at(z) + (size_t)blockIdx.y * n * m;
   const int i0 = blockIdx.x * 64;
   const int k0 = blockIdx.y * chunk;
   const int k1 = min(n, k0 + chunk);
@@ -134,24 +132,24 @@ __global__ void __launch_bounds__(256) k_si_gemm(CPtrs G, CPtrs X, Ptrs Out, int
   }
 }
 
-__global__ void k_si_sum_split(Ptrs part, Ptrs out, int S, long long nm) {
+__global__ void k_si_sum_split(PSet part, PSet out, int S, long long nm) {
   const int z = blockIdx.z;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
        e += (long long)gridDim.x * blockDim.x) {
     double v = 0.0;
-    for (int s = 0; s < S; ++s) v += part.p[z][s * nm + e];
-    out.p[z][e] = v;
+    for (int s = 0; s < S; ++s) v += part.at(z)[s * nm + e];
+    out.at(z)[e] = v;
   }
 }
 
 // Cp[c] = A[rows of chunk c]^T B[same rows]   (m x m, row-major a*m + b)
 template <typename Acc>
-__global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int n, int m, int sym) {
+__global__ void __launch_bounds__(256) k_si_gram(PSet A, PSet B, PSet Cp, int n, int m, int sym) {
   __shared__ Acc As[16][kSiMaxBlock + 1];
   __shared__ Acc Bs[16][kSiMaxBlock + 1];
   const int z = blockIdx.z, c = blockIdx.x;
-  const double *a = A.p[z];
-  const double *b = B.p[z];
+  const double *a = A.at(z);
+  const double *b = B.at(z);
   const int r0 = c * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
   const int ta = threadIdx.x >> 4, tb = threadIdx.x & 15;
   constexpr int U = kSiMaxBlock / 16;   // 6 x 6 outputs per thread
@@ -184,7 +182,7 @@ __global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int 
     }
     __syncthreads();
   }
-  double *out = Cp.p[z] + (size_t)c * m * m;
+  double *out = Cp.at(z) + (size_t)c * m * m;
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -197,14 +195,14 @@ __global__ void __launch_bounds__(256) k_si_gram(CPtrs A, CPtrs B, Ptrs Cp, int 
 // C = sum over row chunks of the Gram partials (fixed order), symmetrised.
 // sym: the partials hold only the upper tiles (A^T A).  ns: write instead the
 // Newton-Schulz polish W = (3 I - C) / 2 (column-major, = row-major by symmetry).
-__global__ void k_si_gram_reduce(CPtrs Cp, Ptrs C, int nchunks, int m, int sym, int ns) {
+__global__ void k_si_gram_reduce(PSet Cp, PSet C, int nchunks, int m, int sym, int ns) {
   const int z = blockIdx.z;
   const long long mm = (long long)m * m;
   constexpr int U = kSiMaxBlock / 16;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int a = e / m, b = e % m;
     if (b < a) continue;
-    const double *src = Cp.p[z];
+    const double *src = Cp.at(z);
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     double sv;
     if (sym) {
@@ -236,8 +234,8 @@ __global__ void k_si_gram_reduce(CPtrs Cp, Ptrs C, int nchunks, int m, int sym, 
       sv = 0.5 * ((v0 + v1) + (w0 + w1));
     }
     if (ns) sv = (a == b ? 1.5 : 0.0) - 0.5 * sv;
-    C.p[z][a * m + b] = sv;
-    C.p[z][b * m + a] = sv;
+    C.at(z)[a * m + b] = sv;
+    C.at(z)[b * m + a] = sv;
   }
 }
 
@@ -246,7 +244,7 @@ __global__ void k_si_gram_reduce(CPtrs Cp, Ptrs C, int nchunks, int m, int sym, 
 // orthonormal up to FP32 accuracy: C_hat = diag(d) C diag(d) + shift I = R^T R,
 // d_j = 1 / sqrt(C_jj).  Used for the iterations between Rayleigh-Ritz steps,
 // where an approximately orthonormal basis is all the power iteration needs.
-__global__ void __launch_bounds__(kCholThreads) k_si_chol32(CPtrs Cin, int m, float shift, Ptrs Wout,
+__global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, float shift, PSet Wout,
                                                             int *flag) {
   extern __shared__ float shf[];
   const int ld = m + 1;
@@ -257,13 +255,13 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(CPtrs Cin, int m, fl
   const int z = blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    const double cjj = Cin.p[z][(size_t)j * m + j];
+    const double cjj = Cin.at(z)[(size_t)j * m + j];
     d[j] = (cjj > 0.0 && isfinite(cjj)) ? (float)rsqrt_fp64(cjj) : 1.0f;
   }
   __syncthreads();
   for (int a = ty; a < m; a += 16)
     for (int b = tx; b < m; b += 16)
-      C[a * ld + b] = (float)Cin.p[z][(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? shift : 0.0f);
+      C[a * ld + b] = (float)Cin.at(z)[(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? shift : 0.0f);
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
@@ -300,7 +298,7 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(CPtrs Cin, int m, fl
       for (int b = i + tx; b < m; b += 16) Z[a * ld + b] = fmaf(-C[a * ld + i], Z[i * ld + b], Z[a * ld + b]);
     __syncthreads();
   }
-  double *W = Wout.p[z];
+  double *W = Wout.at(z);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int c = e / m, j = e % m;           // W[j + c m]
     W[e] = (j <= c) ? (double)Z[j * ld + c] * (double)d[j] : 0.0;
@@ -310,7 +308,7 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(CPtrs Cin, int m, fl
 // Shifted, column-scaled Cholesky of a block's Gram matrix C and the rotation
 // W = diag(d) R^-1 (column-major) such that Y W is orthonormal:
 //   C_hat = diag(d) C diag(d) + shift I = R^T R,  d_j = 1 / sqrt(C_jj).
-__global__ void __launch_bounds__(kCholThreads) k_si_chol(CPtrs Cin, int m, double shift, Ptrs Wout,
+__global__ void __launch_bounds__(kCholThreads) k_si_chol(PSet Cin, int m, double shift, PSet Wout,
                                                           int *flag) {
   extern __shared__ double sh[];
   const int ld = m + 1;
@@ -320,7 +318,7 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol(CPtrs Cin, int m, doub
   double *rinv = d + m;           // m: 1 / R_jj
   const int z = blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) C[(e / m) * ld + e % m] = Cin.p[z][e];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) C[(e / m) * ld + e % m] = Cin.at(z)[e];
   __syncthreads();
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     const double cjj = C[j * ld + j];
@@ -369,7 +367,7 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol(CPtrs Cin, int m, doub
       for (int b = i + tx; b < m; b += 16) Z[a * ld + b] = fma(-C[a * ld + i], Z[i * ld + b], Z[a * ld + b]);
     __syncthreads();
   }
-  double *W = Wout.p[z];
+  double *W = Wout.at(z);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int c = e / m, j = e % m;           // W[j + c m]
     W[e] = (j <= c) ? Z[j * ld + c] * d[j] : 0.0;
@@ -414,7 +412,7 @@ __device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &
   s = t * c;
 }
 
-__global__ void __launch_bounds__(512) k_si_jacobi(CPtrs Cin, int m, Ptrs Wout, Ptrs theta, int *flag,
+__global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, PSet theta, int *flag,
                                                    int *sweeps) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -442,7 +440,7 @@ __global__ void __launch_bounds__(512) k_si_jacobi(CPtrs Cin, int m, Ptrs Wout, 
   for (int e = threadIdx.x; e < (s1 - s0) * 2 * m; e += blockDim.x) {
     const int sl = s0 + e / (2 * m), tb = (e / m) & 1, c = e % m;
     const int idx = tb == 0 ? sl : m - 1 - sl;
-    ROW(0, sl, tb)[c] = Cin.p[z][(size_t)idx * m + c];
+    ROW(0, sl, tb)[c] = Cin.at(z)[(size_t)idx * m + c];
   }
   for (int e = threadIdx.x; e < (v1 - v0) * m; e += blockDim.x) {
     const int rl = e / m, c = e % m;
@@ -591,20 +589,20 @@ __global__ void __launch_bounds__(512) k_si_jacobi(CPtrs Cin, int m, Ptrs Wout, 
       const double tj = diag[j];
       rk += (tj > ti) || (tj == ti && j < i);
     }
-    if (rank == 0) theta.p[z][rk] = ti;
-    for (int row = v0; row < v1; ++row) Wout.p[z][(size_t)rk * m + row] = V[(row - v0) * m + i];
+    if (rank == 0) theta.at(z)[rk] = ti;
+    for (int row = v0; row < v1; ++row) Wout.at(z)[(size_t)rk * m + row] = V[(row - v0) * m + i];
   }
   cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 // Out = A . W  (A, Out n x m column-major; W m x m column-major: W[j + c m])
 // tri: W is upper triangular (W[j, c] = 0 for j > c), so j-blocks past the tile's last column are skipped
-__global__ void __launch_bounds__(256) k_si_rotate(CPtrs A, CPtrs W, Ptrs Out, int n, int m, int tri) {
+__global__ void __launch_bounds__(256) k_si_rotate(PSet A, PSet W, PSet Out, int n, int m, int tri) {
   __shared__ double As[32][33];
   __shared__ double Ws[32][33];
   const int z = blockIdx.z;
-  const double *a = A.p[z];
-  const double *w = W.p[z];
+  const double *a = A.at(z);
+  const double *w = W.at(z);
   const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -632,17 +630,17 @@ __global__ void __launch_bounds__(256) k_si_rotate(CPtrs A, CPtrs W, Ptrs Out, i
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int c = c0 + ty + 8 * u;
-      if (c < m) Out.p[z][(size_t)c * n + i] = acc[u];
+      if (c < m) Out.at(z)[(size_t)c * n + i] = acc[u];
     }
   }
 }
 
 // res[i] = ||Y_i - theta_i X_i|| / |theta_0|, i < k
-__global__ void k_si_residual(CPtrs X, CPtrs Y, CPtrs theta, Ptrs res, int n, int k) {
+__global__ void k_si_residual(PSet X, PSet Y, PSet theta, PSet res, int n, int k) {
   const int z = blockIdx.z, i = blockIdx.x;
-  const double th = theta.p[z][i];
-  const double *x = X.p[z] + (size_t)i * n;
-  const double *y = Y.p[z] + (size_t)i * n;
+  const double th = theta.at(z)[i];
+  const double *x = X.at(z) + (size_t)i * n;
+  const double *y = Y.at(z) + (size_t)i * n;
   double v = 0.0;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const double d = y[r] - th * x[r];
@@ -655,26 +653,34 @@ __global__ void k_si_residual(CPtrs X, CPtrs Y, CPtrs theta, Ptrs res, int n, in
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-    res.p[z][i] = sqrt(s) / fabs(theta.p[z][0]);
+    res.at(z)[i] = sqrt(s) / fabs(theta.at(z)[0]);
   }
 }
 
 // G (n x n) into an m x m zero-padded square (m = n or n + 1) for the direct Jacobi path.
-__global__ void k_si_copy_square(CPtrs G, Ptrs out, int n, int m) {
+__global__ void k_si_copy_square(PSet G, PSet out, int n, int m) {
   const int z = blockIdx.z;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int a = e / m, b = e % m;
-    out.p[z][e] = (a < n && b < n) ? G.p[z][a * n + b] : 0.0;
+    out.at(z)[e] = (a < n && b < n) ? G.at(z)[a * n + b] : 0.0;
   }
 }
 
 // X[:, c] = first n rows of W[:, c] for c < k
-__global__ void k_si_take(CPtrs W, Ptrs X, int n, int m, int k) {
+__global__ void k_si_take(PSet W, PSet X, int n, int m, int k) {
   const int z = blockIdx.z;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += gridDim.x * blockDim.x) {
     const int c = e / n, r = e % n;
-    X.p[z][(size_t)c * n + r] = W.p[z][(size_t)c * m + r];
+    X.at(z)[(size_t)c * n + r] = W.at(z)[(size_t)c * m + r];
   }
+}
+
+// Copy of problem z's n x m block from src to dst (final placement of Ritz vectors).
+__global__ void k_si_copy(PSet src, PSet dst, long long nm) {
+  const int z = blockIdx.z;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
+       e += (long long)gridDim.x * blockDim.x)
+    dst.at(z)[e] = src.at(z)[e];
 }
 
 // ---- host helpers ----
@@ -683,6 +689,8 @@ struct Layout {
   int S, NC, m;
   long long nm, mm;
   long long per;   // doubles per problem
+  // slot offsets (doubles) inside a problem's workspace
+  long long oY, oZ, oX, oYp, oCp, oC, oW, oRes, oTh;
 };
 
 Layout layout(int P, int n, int m) {
@@ -694,46 +702,43 @@ Layout layout(int P, int n, int m) {
   L.S = std::max(1, std::min(kSplitMax, (2 * 152 + tiles * P - 1) / std::max(1, tiles * P)));
   while (L.S > 1 && (n + L.S - 1) / L.S < 64) --L.S;
   L.NC = std::min(kChunkMax, (n + kRowsPerChunk - 1) / kRowsPerChunk);
-  L.per = L.nm * (2 + kSplitMax) + L.mm * (kChunkMax + 2) + 2 * m + 64;
+  auto up = [](long long v) { return (v + 31) / 32 * 32; };   // 256-byte aligned slots
+  long long o = 0;
+  L.oY = o; o += up(L.nm);
+  L.oZ = o; o += up(L.nm);
+  L.oX = o; o += up(L.nm);
+  L.oYp = o; o += up(kSplitMax * L.nm);
+  L.oCp = o; o += up(kChunkMax * L.mm);
+  L.oC = o; o += up(L.mm);
+  L.oW = o; o += up(L.mm);
+  L.oRes = o; o += up(m);
+  L.oTh = o; o += up(m);
+  L.per = o;
   return L;
 }
 
 struct Bufs {
-  double *Y[kSiMaxBatch], *Z[kSiMaxBatch], *Yp[kSiMaxBatch], *Cp[kSiMaxBatch], *C[kSiMaxBatch];
-  double *W[kSiMaxBatch], *res[kSiMaxBatch];
+  PSet Y, Z, X, Yp, Cp, C, W, res, th;
   int *flag, *sweeps;
 };
 
-// per problem: Y, Z (n m each) | split partials (kSplitMax n m) | Gram partials
-// (kChunkMax m m) | C (m m) | W (m m) | res (m)
 Bufs carve(double *work, int P, const Layout &L) {
-  Bufs B{};
-  for (int p = 0; p < P; ++p) {
-    double *base = work + p * L.per;
-    B.Y[p] = base;
-    B.Z[p] = base + L.nm;
-    B.Yp[p] = base + 2 * L.nm;
-    B.Cp[p] = base + (2 + kSplitMax) * L.nm;
-    B.C[p] = B.Cp[p] + kChunkMax * L.mm;
-    B.W[p] = B.C[p] + L.mm;
-    B.res[p] = B.W[p] + L.mm;
-  }
-  B.flag = reinterpret_cast<int *>(work + P * L.per);
+  Bufs B;
+  B.Y = pset_linear(work + L.oY, L.per);
+  B.Z = pset_linear(work + L.oZ, L.per);
+  B.X = pset_linear(work + L.oX, L.per);
+  B.Yp = pset_linear(work + L.oYp, L.per);
+  B.Cp = pset_linear(work + L.oCp, L.per);
+  B.C = pset_linear(work + L.oC, L.per);
+  B.W = pset_linear(work + L.oW, L.per);
+  B.res = pset_linear(work + L.oRes, L.per);
+  B.th = pset_linear(work + L.oTh, L.per);
+  B.flag = reinterpret_cast<int *>(work + (long long)P * L.per);
   B.sweeps = B.flag + 2;
   return B;
 }
 
-template <typename T>
-CPtrs cp_of(T *const *a, int P) {
-  CPtrs c{};
-  for (int p = 0; p < P; ++p) c.p[p] = a[p];
-  return c;
-}
-Ptrs p_of(double *const *a, int P) {
-  Ptrs c{};
-  for (int p = 0; p < P; ++p) c.p[p] = a[p];
-  return c;
-}
+bool same(const PSet &a, const PSet &b) { return a.b0 == b.b0 && a.b1 == b.b1 && a.stride == b.stride; }
 
 size_t jacobi_smem(int m) {
   const int half = m / 2;
@@ -757,12 +762,12 @@ cudaError_t set_attrs() {
   return cudaSuccess;
 }
 
-int grid_1d(long long count) {
+int grid_1d(long long count, int P) {
   long long b = (count + 255) / 256;
-  return (int)std::max<long long>(1, std::min<long long>(b, 152 * 4));
+  return (int)std::max<long long>(1, std::min<long long>(b, (152 * 4 + P - 1) / P));
 }
 
-cudaError_t launch_jacobi(CPtrs C, int m, Ptrs W, Ptrs theta, int *flag, int *sweeps, int P,
+cudaError_t launch_jacobi(PSet C, int m, PSet W, PSet theta, int *flag, int *sweeps, int P,
                           cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(kCluster, 1, P);
@@ -785,20 +790,30 @@ long long si_workspace_doubles(int P, int n, int m) {
   return layout(P, n, m).per * P + 64;
 }
 
+int jacobi_block(int n) {
+  const int m = n + (n & 1);
+  return m < 4 ? 4 : m;
+}
+
+SiOut si_outputs(double *work, int P, int n, int m) {
+  const Layout L = layout(P, n, m);
+  Bufs B = carve(work, P, L);
+  return SiOut{B.X, B.th};
+}
+
 cudaError_t jacobi_full(const SiBatch &b, double *work, cudaStream_t s, long long *launches) {
   cudaError_t e = set_attrs();
   if (e) return e;
   const int n = b.n, P = b.P;
   int m = n + (n & 1);              // the round-robin pairing needs an even size
   if (m < 4) m = 4;                 // and at least two pairs
-  if (m > kSiMaxBlock || b.k > n) return cudaErrorInvalidValue;
+  if (m > kSiMaxBlock || b.k > n || P > 65535) return cudaErrorInvalidValue;
   const Layout L = layout(P, n, m);
   Bufs B = carve(work, P, L);
   if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
-  k_si_copy_square<<<dim3(grid_1d((long long)m * m), 1, P), 256, 0, s>>>(cp_of(b.G, P), p_of(B.C, P), n, m);
-  if ((e = launch_jacobi(cp_of(B.C, P), m, p_of(B.W, P), p_of(b.theta, P), B.flag, B.sweeps, P, s)))
-    return e;
-  k_si_take<<<dim3(grid_1d((long long)n * b.k), 1, P), 256, 0, s>>>(cp_of(B.W, P), p_of(b.X, P), n, m, b.k);
+  k_si_copy_square<<<dim3(grid_1d((long long)m * m, P), 1, P), 256, 0, s>>>(b.G, B.C, n, m);
+  if ((e = launch_jacobi(B.C, m, B.W, B.th, B.flag, B.sweeps, P, s))) return e;
+  k_si_take<<<dim3(grid_1d((long long)n * b.k, P), 1, P), 256, 0, s>>>(B.W, B.X, n, m, b.k);
   *launches += 3;
   return cudaGetLastError();
 }
@@ -808,59 +823,54 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   cudaError_t e = set_attrs();
   if (e) return e;
   const int P = b.P, n = b.n, m = b.m, k = b.k;
-  if (P < 1 || P > kSiMaxBatch || m > kSiMaxBlock || m > n || k > m || (m & 1))
+  if (P < 1 || P > 65535 || m > kSiMaxBlock || m > n || k > m || (m & 1))
     return cudaErrorInvalidValue;
   const Layout L = layout(P, n, m);
   Bufs B = carve(work, P, L);
-  double *X[kSiMaxBatch], *Y[kSiMaxBatch], *Z[kSiMaxBatch];
-  for (int p = 0; p < P; ++p) {
-    X[p] = b.X[p];
-    Y[p] = B.Y[p];
-    Z[p] = B.Z[p];
-  }
+  PSet X = B.X, Y = B.Y, Z = B.Z;
   const dim3 gz(1, 1, P);
   const dim3 grot((n + 31) / 32, (m + 31) / 32, P);
   const int chunk = ((n + L.S - 1) / L.S + 15) / 16 * 16;
   const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16;
   long long nl = 0;
 
-  auto gemm = [&](double *const *src, double *const *dst) {
+  auto gemm = [&](PSet src, PSet dst) {
     if (L.S == 1) {
-      k_si_gemm<<<dim3((n + 63) / 64, 1, P), 256, 0, s>>>(cp_of(b.G, P), cp_of(src, P), p_of(dst, P), n, m, chunk);
+      k_si_gemm<<<dim3((n + 63) / 64, 1, P), 256, 0, s>>>(b.G, src, dst, n, m, chunk);
       nl += 1;
     } else {
-      k_si_gemm<<<dim3((n + 63) / 64, L.S, P), 256, 0, s>>>(cp_of(b.G, P), cp_of(src, P), p_of(B.Yp, P), n, m, chunk);
-      k_si_sum_split<<<dim3(grid_1d(L.nm), 1, P), 256, 0, s>>>(p_of(B.Yp, P), p_of(dst, P), L.S, L.nm);
+      k_si_gemm<<<dim3((n + 63) / 64, L.S, P), 256, 0, s>>>(b.G, src, B.Yp, n, m, chunk);
+      k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, L.S, L.nm);
       nl += 2;
     }
   };
   // C = A^T B (m x m), symmetrised; ns: write the Newton-Schulz polish (3I - C)/2 instead
-  auto gram = [&](double *const *A, double *const *Bm, bool sym, bool f32, bool ns) {
+  auto gram = [&](PSet A, PSet Bm, bool sym, bool f32, bool ns) {
     if (f32)
-      k_si_gram<float><<<dim3(L.NC, 1, P), 256, 0, s>>>(cp_of(A, P), cp_of(Bm, P), p_of(B.Cp, P), n, m, sym);
+      k_si_gram<float><<<dim3(L.NC, 1, P), 256, 0, s>>>(A, Bm, B.Cp, n, m, sym);
     else
-      k_si_gram<double><<<dim3(L.NC, 1, P), 256, 0, s>>>(cp_of(A, P), cp_of(Bm, P), p_of(B.Cp, P), n, m, sym);
-    k_si_gram_reduce<<<dim3(grid_1d(L.mm), 1, P), 256, 0, s>>>(cp_of(B.Cp, P), p_of(B.C, P), L.NC, m, sym, ns);
+      k_si_gram<double><<<dim3(L.NC, 1, P), 256, 0, s>>>(A, Bm, B.Cp, n, m, sym);
+    k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, B.C, L.NC, m, sym, ns);
     nl += 2;
   };
   // one CholeskyQR pass in FP32 (Gram and factor), rotation in FP64: dst = src W
-  auto cholqr32 = [&](double *const *src, double *const *dst, float sh) {
+  auto cholqr32 = [&](PSet src, PSet dst, float sh) {
     gram(src, src, true, true, false);
-    k_si_chol32<<<gz, kCholThreads, chol32_smem(m), s>>>(cp_of(B.C, P), m, sh, p_of(B.W, P), B.flag);
-    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.W, P), p_of(dst, P), n, m, 1);
+    k_si_chol32<<<gz, kCholThreads, chol32_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
+    k_si_rotate<<<grot, 256, 0, s>>>(src, B.W, dst, n, m, 1);
     nl += 2;
   };
   // one CholeskyQR pass in FP64 (robust for any conditioning with the shift)
-  auto cholqr64 = [&](double *const *src, double *const *dst, double sh) {
+  auto cholqr64 = [&](PSet src, PSet dst, double sh) {
     gram(src, src, true, false, false);
-    k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(cp_of(B.C, P), m, sh, p_of(B.W, P), B.flag);
-    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.W, P), p_of(dst, P), n, m, 1);
+    k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
+    k_si_rotate<<<grot, 256, 0, s>>>(src, B.W, dst, n, m, 1);
     nl += 2;
   };
   // FP64 Newton-Schulz step towards orthonormality: dst = src (3I - src^T src) / 2
-  auto polish = [&](double *const *src, double *const *dst) {
+  auto polish = [&](PSet src, PSet dst) {
     gram(src, src, true, false, true);
-    k_si_rotate<<<grot, 256, 0, s>>>(cp_of(src, P), cp_of(B.C, P), p_of(dst, P), n, m, 0);
+    k_si_rotate<<<grot, 256, 0, s>>>(src, B.C, dst, n, m, 0);
     nl += 1;
   };
   // dst = orth(src) through tmp (src is overwritten).  Until the first
@@ -868,7 +878,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   // conditioned: shifted CholeskyQR3 in FP64.  Afterwards the basis holds Ritz
   // vectors, G X is X Theta up to the residual, its column-scaled Gram matrix is
   // close to I, and two FP32 CholeskyQR passes suffice for the power iteration.
-  auto orth = [&](double **src, double **tmp, double **dst, bool after_rr) {
+  auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) {
     if (after_rr) {
       cholqr32(src, tmp, 0.0f);
       cholqr32(tmp, dst, 0.0f);
@@ -878,18 +888,13 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       cholqr64(src, dst, 0.0);
     }
   };
-  // x = FP64-orthonormal x (two Newton-Schulz steps through tmp)
-  auto polish2 = [&](double **x, double **tmp) {
-    polish(x, tmp);
-    polish(tmp, x);
-  };
 
   if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
-  k_si_init<<<dim3(grid_1d(L.nm), 1, P), 256, 0, s>>>(p_of(X, P), cp_of(b.warm, P), b.kw, n, m);
+  k_si_init<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(X, b.warm, b.has_warm ? 1 : 0, b.kw, n, m);
   nl += 1;
   cholqr32(X, Z, 0.0f);             // a random start is well conditioned
   cholqr32(Z, Y, 0.0f);
-  for (int p = 0; p < P; ++p) std::swap(X[p], Y[p]);
+  std::swap(X, Y);
 
   res->converged = false;
   res->rr = 0;
@@ -899,28 +904,28 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
-    if (check) polish2(X, Z);       // the Rayleigh-Ritz step needs an FP64-orthonormal basis
+    if (check) {                    // the Rayleigh-Ritz step needs an FP64-orthonormal basis
+      polish(X, Z);
+      polish(Z, X);
+    }
     gemm(X, Y);                     // Y = G X
     ++it;
     if (check) {
       gram(X, Y, false, false, false);   // H = X^T G X
-      if ((e = launch_jacobi(cp_of(B.C, P), m, p_of(B.W, P), p_of(b.theta, P), B.flag, B.sweeps, P, s)))
-        return e;
-      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(X, P), cp_of(B.W, P), p_of(Z, P), n, m, 0);
-      for (int p = 0; p < P; ++p) std::swap(X[p], Z[p]);
-      k_si_rotate<<<grot, 256, 0, s>>>(cp_of(Y, P), cp_of(B.W, P), p_of(Z, P), n, m, 0);
-      for (int p = 0; p < P; ++p) std::swap(Y[p], Z[p]);
-      k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(cp_of(X, P), cp_of(Y, P), cp_of(b.theta, P), p_of(B.res, P), n, k);
+      if ((e = launch_jacobi(B.C, m, B.W, B.th, B.flag, B.sweeps, P, s))) return e;
+      k_si_rotate<<<grot, 256, 0, s>>>(X, B.W, Z, n, m, 0);
+      std::swap(X, Z);
+      k_si_rotate<<<grot, 256, 0, s>>>(Y, B.W, Z, n, m, 0);
+      std::swap(Y, Z);
+      k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, n, k);
       nl += 4;
       ++res->rr;
-      for (int p = 0; p < P; ++p) {
-        if ((e = cudaMemcpyAsync(hres.data() + (size_t)p * k, B.res[p], sizeof(double) * k,
-                                 cudaMemcpyDeviceToHost, s)))
-          return e;
-        if ((e = cudaMemcpyAsync(hth.data() + (size_t)p * m, b.theta[p], sizeof(double) * m,
-                                 cudaMemcpyDeviceToHost, s)))
-          return e;
-      }
+      if ((e = cudaMemcpy2DAsync(hres.data(), sizeof(double) * k, B.res.at(0), sizeof(double) * L.per,
+                                 sizeof(double) * k, P, cudaMemcpyDeviceToHost, s)))
+        return e;
+      if ((e = cudaMemcpy2DAsync(hth.data(), sizeof(double) * m, B.th.at(0), sizeof(double) * L.per,
+                                 sizeof(double) * m, P, cudaMemcpyDeviceToHost, s)))
+        return e;
       int hflag[2];
       if ((e = cudaMemcpyAsync(hflag, B.flag, sizeof(hflag), cudaMemcpyDeviceToHost, s))) return e;
       if ((e = cudaStreamSynchronize(s))) return e;
@@ -947,11 +952,11 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     orth(Y, Z, X, res->rr > 0);     // X = orth(G X)
   }
   res->iterations = it;
-  // the Ritz vectors must end in the caller's X buffers
-  for (int p = 0; p < P; ++p)
-    if (X[p] != b.X[p] &&
-        (e = cudaMemcpyAsync(b.X[p], X[p], sizeof(double) * L.nm, cudaMemcpyDeviceToDevice, s)))
-      return e;
+  // the Ritz vectors end in the workspace's X slot
+  if (!same(X, B.X)) {
+    k_si_copy<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(X, B.X, L.nm);
+    nl += 1;
+  }
   *launches += nl;
   return cudaGetLastError();
 }

@@ -2,31 +2,42 @@
 // semi-definite environment matrices: block subspace iteration with
 // Rayleigh-Ritz, where the small projected problem is diagonalised by a
 // parallel-ordered two-sided Jacobi method (Sec. II.B, Eqs. 5-6: rotations of
-// 2x2 blocks, all disjoint pairs of a round at once, pairs rotated between
+// 2x2 blocks, all disjoint pairs of a round at once, rows exchanged between
 // rounds so that every pair meets once per sweep).
+//
+// A batch is P problems of the same size n (the two environments of each of
+// G instances are problems 2i and 2i + 1).  All per-problem buffers live in one
+// workspace at a fixed stride, so a batch of any size costs the same launches.
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace hotrg {
 
-constexpr int kSiMaxBatch = 8;     // problems per call (the two environments of a step)
 constexpr int kSiMaxBlock = 96;    // largest Rayleigh-Ritz block / direct-Jacobi size
 
 struct SiBatch {
-  int P;                           // number of problems
-  int n;                           // matrix size (same for all problems)
-  int k;                           // wanted leading eigenpairs
-  int m;                           // block size (k <= m <= min(n, kSiMaxBlock))
-  const double *G[kSiMaxBatch];    // symmetric n x n (row- or column-major)
-  double *X[kSiMaxBatch];          // in/out: n x m column-major; on return the leading
-                                   // columns hold the Ritz vectors, descending
-  double *theta[kSiMaxBatch];      // out: m Ritz values, descending
-  const double *warm[kSiMaxBatch]; // optional n x kw column-major start vectors (or null)
-  int kw;                          // number of warm-start columns
+  int P;                 // number of problems
+  int n;                 // matrix size (same for all problems)
+  int k;                 // wanted leading eigenpairs
+  int m;                 // block size (k <= m <= min(n, kSiMaxBlock), even)
+  PSet G;                // symmetric n x n matrix of problem z
+  PSet warm;             // optional n x kw column-major start vectors of problem z
+  bool has_warm;
+  int kw;
 };
 
-// Workspace (doubles) needed for a batch of P problems of size n with block m.
+// Where a solve leaves its results inside the workspace: Ritz vectors of
+// problem z at X.at(z) (n x m column-major, leading columns descending) and Ritz
+// values at theta.at(z) (m values, descending).
+struct SiOut {
+  PSet X, theta;
+};
+SiOut si_outputs(double *work, int P, int n, int m);
+
+// Workspace (doubles) for P problems of size n with block m.
 long long si_workspace_doubles(int P, int n, int m);
 
 struct SiResult {
@@ -36,8 +47,6 @@ struct SiResult {
   bool converged;
 };
 
-class StageHook;
-
 // Runs the solver on stream s (synchronises it once per convergence check).
 // `tol` is the residual target relative to the largest Ritz value.  Returns a
 // CUDA error code; `res` reports convergence (the caller decides on fallback).
@@ -45,8 +54,10 @@ class StageHook;
 cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, cudaStream_t s,
                      SiResult *res, long long *launches);
 
-// Direct two-sided Jacobi on whole small matrices (n <= kSiMaxBlock): G_p is
-// copied, diagonalised, and X_p / theta_p receive all n eigenpairs, descending.
+// Direct two-sided Jacobi on whole small matrices (n <= kSiMaxBlock): G is
+// copied (zero-padded to the even size jacobi_block(n)), diagonalised, and the
+// k leading eigenpairs land in si_outputs(work, P, n, jacobi_block(n)).
+int jacobi_block(int n);
 cudaError_t jacobi_full(const SiBatch &b, double *work, cudaStream_t s, long long *launches);
 
 }  // namespace hotrg

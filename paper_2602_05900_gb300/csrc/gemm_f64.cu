@@ -4,7 +4,7 @@
 // C(m, n) = sum_k A(m, k) B(n, k), where A(m, k) = A[am(m) + ak(k)] and so on
 // for B and C (see IdxMap).  64 x 64 output tile per 256-thread block, 4 x 4
 // outputs per thread, K staged through shared memory in chunks of 16 with a
-// register prefetch of the next chunk.
+// register prefetch of the next chunk; grid.z runs over the instances of a batch.
 #include "common.cuh"
 
 namespace hotrg {
@@ -23,6 +23,10 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(MappedGemm g) {
   const int tx = tid & 15, ty = tid >> 4;
   const long long m0 = (long long)blockIdx.x * BM;
   const long long n0 = (long long)blockIdx.y * BN;
+  // instance of the batch
+  g.A += blockIdx.z * g.bA;
+  g.B += blockIdx.z * g.bB;
+  g.C += blockIdx.z * g.bC;
 
   if (tid < BM) {
     long long m = m0 + tid;
@@ -125,8 +129,9 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(MappedGemm g) {
 
 cudaError_t gemm_f64(const MappedGemm &g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
+            (unsigned)(g.batch < 1 ? 1 : g.batch));
+  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
   const bool ka = (g.ak.s0 == 1), kb = (g.bk.s0 == 1);
   if (ka && kb) k_gemm_f64<true, true><<<grid, NT, 0, s>>>(g);
   else if (ka) k_gemm_f64<true, false><<<grid, NT, 0, s>>>(g);

@@ -4,7 +4,7 @@
 //
 //   environment partials  A_L, B_L, A_R, B_R   (four GEMMs, K = Dx*Dy)
 //   Gram combine          G_L, G_R              (two GEMMs, K = Dy^2), FP64 symmetrise
-//   eigendecomposition    top D'(+1) pairs of G_L and G_R (FP64, cuSOLVER)
+//   eigendecomposition    top D'(+1) pairs of G_L and G_R (FP64)
 //   isometry choice       smaller discarded weight, sign-fixed U   (device)
 //   projection chain      P = U.T, Q = P.T, T' = Q.U               (three GEMMs)
 //   rescale               c = max|T'|, T' /= c, logsum += ln(c) / 2^n (FP64)
@@ -12,10 +12,19 @@
 // An X step runs the same chain on the strided view T[y,y',x,x'] and writes
 // its result back through the transposed view; nothing is copied to switch
 // directions.
+//
+// A context holds one or more instances.  Instances with the same (D0, D_cut)
+// have the same bond dimensions after every step, so they form a group whose
+// buffers sit at a fixed per-instance stride; every kernel of the step runs
+// once per group over all of its instances (grid.z / grid.y batching), and the
+// eigensolver treats the group's 2G environments as one batch.  A context made
+// by hotrg_create is a single group of one instance.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -30,7 +39,11 @@ using namespace hotrg;
 namespace {
 
 constexpr int kMaxSteps = 256;
-constexpr int kRecord = 8;  // side, eps_L, eps_R, cut_gap, trace_G, ln_c, -, -
+constexpr int kRecord = 8;       // side, eps_L, eps_R, cut_gap, trace_G, ln_c, -, -
+constexpr int kScal = 8;         // logsum, max scratch, tr G_L, tr G_R, trace T, -, -, -
+constexpr int kMaxInstances = 4096;
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
 // Records CUDA events around each stage while enabled; the intervals are
 // resolved into milliseconds once the stream has passed them.
@@ -118,37 +131,52 @@ class Profiler : public StageHook {
   cudaEvent_t open_[HOTRG_NSTAGES] = {};
 };
 
+// Per-step diagnostics that are the same for every instance of a group.
+struct GroupStep {
+  hotrg_step_info_t info;   // dir, Dx, Dy, Dn, eig_path, eig_iters, eig_residual
+  int spec_count;
+  int n, dn;                // shape of U
+};
+
+// Instances that share (D0, D_cut) and so every bond dimension.  Buffers hold
+// G instances at the strides below (elements, multiples of 32 doubles).
+struct Group {
+  int D0 = 0, D_cut = 0, Dm = 0, G = 0;
+  int dx = 0, dy = 0;
+  std::vector<int> members;       // instance ids, in creation order
+  long long sT = 0;               // T, Tn, partials, Gram matrices: Dm^4
+  long long sU = 0;               // U: Dm^2 (D_cut + 1)
+  long long sUp = 0;              // previous isometry per direction: Dm^2 D_cut
+  long long sW = 0;               // library-fallback eigenvalues: Dm^2
+  long long sP = 0;               // FP64 P and Q: D_cut Dm^4
+  long long sRec = 0, sSpec = 0;  // step records / spectra per instance
+  double *T = nullptr, *Tn = nullptr;
+  double *AL = nullptr, *BL = nullptr, *AR = nullptr, *BR = nullptr;
+  double *GL = nullptr, *GR = nullptr;
+  double *wL = nullptr, *wR = nullptr;
+  double *U = nullptr, *P = nullptr, *Q = nullptr;
+  double *scal = nullptr;         // kScal per instance
+  double *records = nullptr;      // kMaxSteps x kRecord per instance
+  double *spectra = nullptr;      // kMaxSteps x (D_cut + 1) per instance
+  double *Uprev[2] = {nullptr, nullptr};
+  int nprev[2] = {0, 0}, kprev[2] = {0, 0};
+  TcPath tc;
+  std::vector<GroupStep> steps;
+};
+
 }  // namespace
 
 struct hotrg_ctx {
   Profiler prof;
   cudaStream_t stream = nullptr;
   Eig eig;
-  TcPath tc;
-  int D0 = 0, D_cut = 0, Dm = 0;
   hotrg_prec prec = HOTRG_FP64;
-  int dx = 0, dy = 0, nsteps = 0;
-  int last_n = 0, last_dn = 0;   // shape of U of the last step
-
-  double *T = nullptr, *Tn = nullptr;
-  double *AL = nullptr, *BL = nullptr, *AR = nullptr, *BR = nullptr;
-  double *GL = nullptr, *GR = nullptr;
-  double *wL = nullptr, *wR = nullptr;
-  double *U = nullptr;
-  double *P = nullptr, *Q = nullptr;
-  double *scal = nullptr;      // [0] logsum, [1] max scratch, [2] tr G_L, [3] tr G_R, [4] trace T
+  int nsteps = 0;
+  int n_inst = 0;
+  std::vector<std::unique_ptr<Group>> groups;
+  std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
+  double *si_work = nullptr;                // eigensolver workspace, shared by the groups
   int *err = nullptr;
-  double *records = nullptr;   // kMaxSteps x kRecord
-  double *spectra = nullptr;   // kMaxSteps x (D_cut + 1)
-  std::vector<hotrg_step_info_t> info;
-  std::vector<int> spec_count;
-  // own FP64 eigensolver: workspace, Ritz vectors / values of both sides, and the
-  // last isometry per direction (start vectors of the next step in that direction)
-  double *si_work = nullptr;
-  double *XL = nullptr, *XR = nullptr, *thL = nullptr, *thR = nullptr;
-  double *Uprev[2] = {nullptr, nullptr};
-  int nprev[2] = {0, 0}, kprev[2] = {0, 0};
-
   hotrg_status status = HOTRG_OK;
   std::string msg;
   std::vector<void *> allocs;
@@ -211,6 +239,380 @@ hotrg_status check_flag(hotrg_ctx *c) {
   return HOTRG_OK;
 }
 
+// Device buffers of one group, sized for bond dimensions up to max(D0, D_cut).
+hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
+  const long long Dm = g.Dm, t4 = Dm * Dm * Dm * Dm, nmax = Dm * Dm;
+  const int G = g.G;
+  g.sT = round_up(t4, 32);
+  g.sU = round_up(nmax * (g.D_cut + 1), 32);
+  g.sUp = round_up(nmax * g.D_cut, 32);
+  g.sW = round_up(nmax, 32);
+  g.sP = round_up((long long)g.D_cut * t4, 32);
+  g.sRec = (long long)kMaxSteps * kRecord;
+  g.sSpec = round_up((long long)kMaxSteps * (g.D_cut + 1), 32);
+  hotrg_status s;
+  if ((s = dalloc(c, &g.T, g.sT * G)) || (s = dalloc(c, &g.Tn, g.sT * G)) ||
+      (s = dalloc(c, &g.GL, g.sT * G)) || (s = dalloc(c, &g.GR, g.sT * G)) ||
+      (s = dalloc(c, &g.wL, g.sW * G)) || (s = dalloc(c, &g.wR, g.sW * G)) ||
+      (s = dalloc(c, &g.U, g.sU * G)) || (s = dalloc(c, &g.scal, (long long)kScal * G)) ||
+      (s = dalloc(c, &g.records, g.sRec * G)) || (s = dalloc(c, &g.spectra, g.sSpec * G)) ||
+      (s = dalloc(c, &g.Uprev[0], g.sUp * G)) || (s = dalloc(c, &g.Uprev[1], g.sUp * G)))
+    return s;
+  if (c->prec == HOTRG_FP64) {
+    if ((s = dalloc(c, &g.AL, g.sT * G)) || (s = dalloc(c, &g.BL, g.sT * G)) ||
+        (s = dalloc(c, &g.AR, g.sT * G)) || (s = dalloc(c, &g.BR, g.sT * G)) ||
+        (s = dalloc(c, &g.P, g.sP * G)) || (s = dalloc(c, &g.Q, g.sP * G)))
+      return s;
+  } else {
+    const int r = g.tc.init(c->prec, g.D0, g.D_cut, G, c->stream, c->err);
+    if (r == 2) return fail(c, HOTRG_ENOMEM, "tensor-core operand buffers do not fit");
+    if (r) return fail(c, HOTRG_ECUDA, "tensor-core path initialisation failed");
+  }
+  return HOTRG_OK;
+}
+
+bool valid_prec(hotrg_prec p) {
+  return p == HOTRG_FP64 || p == HOTRG_TF32 || p == HOTRG_BF16X3 || p == HOTRG_BF16X6;
+}
+
+// Shared constructor: n instances, T0s[i] of D0s[i]^4 doubles.
+hotrg_status create_ctx(int n, const double *const *T0s, const int *D0s, const int *Dcuts,
+                        hotrg_prec prec, void *stream, hotrg_ctx **out) {
+  if (!out) return HOTRG_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > kMaxInstances || !T0s || !D0s || !Dcuts || !valid_prec(prec)) return HOTRG_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!T0s[i] || D0s[i] < 1 || D0s[i] > 64 || Dcuts[i] < 1 || Dcuts[i] > 64) return HOTRG_EINVAL;
+  hotrg_ctx *c = new (std::nothrow) hotrg_ctx();
+  if (!c) return HOTRG_ENOMEM;
+  auto bail = [&](hotrg_status s) {
+    hotrg_destroy(c);
+    return s;
+  };
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->prof.stream = c->stream;
+  c->prec = prec;
+  c->n_inst = n;
+  c->where.resize(n);
+  for (int i = 0; i < n; ++i) {
+    int gi = -1;
+    for (int j = 0; j < (int)c->groups.size(); ++j)
+      if (c->groups[j]->D0 == D0s[i] && c->groups[j]->D_cut == Dcuts[i]) gi = j;
+    if (gi < 0) {
+      std::unique_ptr<Group> g(new (std::nothrow) Group());
+      if (!g) return bail(HOTRG_ENOMEM);
+      g->D0 = D0s[i];
+      g->D_cut = Dcuts[i];
+      g->Dm = std::max(D0s[i], Dcuts[i]);
+      g->dx = g->dy = D0s[i];
+      c->groups.push_back(std::move(g));
+      gi = (int)c->groups.size() - 1;
+    }
+    Group &g = *c->groups[gi];
+    c->where[i] = {gi, (int)g.members.size()};
+    g.members.push_back(i);
+  }
+  hotrg_status s;
+  if ((s = dalloc(c, &c->err, 4))) return bail(s);
+  long long si_doubles = 0;
+  for (auto &gp : c->groups) {
+    Group &g = *gp;
+    g.G = (int)g.members.size();
+    if ((s = alloc_group(c, g))) return bail(s);
+    const int nsi = std::max(g.Dm * g.Dm, kSiMaxBlock + 1);
+    si_doubles = std::max(si_doubles, si_workspace_doubles(2 * g.G, nsi, kSiMaxBlock));
+  }
+  if ((s = dalloc(c, &c->si_work, (size_t)si_doubles))) return bail(s);
+  if (int r = c->eig.init(c->stream)) return bail(r == 2 ? HOTRG_ENOMEM : HOTRG_ECUDA);
+  if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) return bail(HOTRG_ECUDA);
+  for (auto &gp : c->groups) {
+    Group &g = *gp;
+    const long long cnt = (long long)g.D0 * g.D0 * g.D0 * g.D0;
+    if (cudaMemsetAsync(g.scal, 0, sizeof(double) * kScal * g.G, c->stream) != cudaSuccess)
+      return bail(HOTRG_ECUDA);
+    for (int j = 0; j < g.G; ++j)
+      if (cudaMemcpyAsync(g.T + j * g.sT, T0s[g.members[j]], sizeof(double) * cnt,
+                          cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return bail(HOTRG_ECUDA);
+    // c_0 = max|T0| with weight 1: the initial tensor is one site
+    if (maxabs_scale_log(g.T, cnt, g.sT, g.scal + 1, kScal, g.scal, kScal, 1.0, nullptr, 0, c->err,
+                         g.G, c->stream) != cudaSuccess)
+      return bail(HOTRG_ECUDA);
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HOTRG_ECUDA);
+  int herr = 0;
+  if (cudaMemcpy(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bail(HOTRG_ECUDA);
+  if (herr) return bail(HOTRG_ENONFINITE);
+  *out = c;
+  return HOTRG_OK;
+}
+
+// One step of every instance of group g (see the file comment).
+hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
+  cudaStream_t st = c->stream;
+  Profiler &pf = c->prof;
+  const int G = g.G;
+
+  // ---- the step's view of the stored tensor T[x,x',y,y'] (shape dx,dx,dy,dy)
+  const bool ydir = (dir == HOTRG_DIR_Y);
+  const int D = ydir ? g.dx : g.dy;     // fused legs
+  const int E = ydir ? g.dy : g.dx;     // contracted legs
+  const long long cx = (long long)g.dx * g.dy * g.dy, cxp = (long long)g.dy * g.dy,
+                  cy = g.dy, cyp = 1;
+  const long long sx = ydir ? cx : cy, sxp = ydir ? cxp : cyp;
+  const long long sy = ydir ? cy : cx, syp = ydir ? cyp : cxp;
+  const int n = D * D;
+  const int Dn = n < g.D_cut ? n : g.D_cut;
+  const long long DE = (long long)D * E, E2 = (long long)E * E, D2 = (long long)D * D;
+  double *rec = g.records + (size_t)step * kRecord;
+  double *spec = g.spectra + (size_t)step * (g.D_cut + 1);
+  const double fD = D, fE = E, fDn = Dn, fG = G;
+  pf.flops(HOTRG_ST_ENV, fG * 4.0 * 2.0 * fD * fD * fD * fE * fE * fE);
+  pf.flops(HOTRG_ST_GRAM, fG * 2.0 * 2.0 * fD * fD * fD * fD * fE * fE);
+  pf.flops(HOTRG_ST_PROJ_P, fG * 2.0 * fDn * fD * fD * fD * fE * fE);
+  pf.flops(HOTRG_ST_PROJ_Q, fG * 2.0 * fDn * fD * fD * fD * fE * fE * fE);
+  pf.flops(HOTRG_ST_PROJ_T, fG * 2.0 * fDn * fDn * fD * fD * fE * fE);
+
+  // ---- a2/a3: environments G_L, G_R ([x1][x2][u1][u2], FP64)
+  const bool tc = (c->prec != HOTRG_FP64);
+  if (tc) {
+    if (g.tc.environment(g.T, g.sT, D, E, sx, sxp, sy, syp, g.GL, g.GR, g.sT, &pf))
+      return fail(c, HOTRG_ECUDA, "tensor-core environment chain failed");
+  } else {
+    // partials written as [x][u][k][k'] for the Gram combine
+    const IdxMap out_m = map2(E, E, (long long)D * E2), out_n = map2(E, 1, E2);
+    struct Part { double *dst; IdxMap row, red; };
+    const Part parts[4] = {
+        {g.AL, map2(E, syp, sx), map2(E, sy, sxp)},    // A_L[x1,k,u1,k']: sum over (x1', y)
+        {g.BL, map2(E, sy, sx), map2(E, syp, sxp)},    // B_L[x2,k,u2,k']: sum over (x2', y')
+        {g.AR, map2(E, syp, sxp), map2(E, sy, sx)},    // A_R[x1',k,u1',k']: sum over (x1, y)
+        {g.BR, map2(E, sy, sxp), map2(E, syp, sx)},    // B_R[x2',k,u2',k']: sum over (x2, y')
+    };
+    pf.begin(HOTRG_ST_ENV);
+    for (const Part &p : parts) {
+      MappedGemm m{(int)DE, (int)DE, (int)DE, g.T, p.row, p.red, g.T, p.row, p.red, p.dst, out_m,
+                   out_n, G, g.sT, g.sT, g.sT};
+      CK_CUDA(c, gemm_f64(m, st));
+    }
+    pf.launched(HOTRG_ST_ENV, 4);
+    pf.end(HOTRG_ST_ENV);
+    // G[x1,x2,u1,u2] = sum_{k,k'} A[x1,u1,k,k'] B[x2,u2,k,k']
+    pf.begin(HOTRG_ST_GRAM);
+    const IdxMap gm = map2(D, D, D2 * D), gn = map2(D, 1, D2);
+    MappedGemm gl{(int)D2, (int)D2, (int)E2, g.AL, map1(E2), map1(1), g.BL, map1(E2), map1(1),
+                  g.GL, gm, gn, G, g.sT, g.sT, g.sT};
+    MappedGemm gr{(int)D2, (int)D2, (int)E2, g.AR, map1(E2), map1(1), g.BR, map1(E2), map1(1),
+                  g.GR, gm, gn, G, g.sT, g.sT, g.sT};
+    CK_CUDA(c, gemm_f64(gl, st));
+    CK_CUDA(c, gemm_f64(gr, st));
+    pf.launched(HOTRG_ST_GRAM, 2);
+  }
+  CK_CUDA(c, symmetrize_trace(g.GL, n, g.sT, g.scal + 2, kScal, G, st));
+  CK_CUDA(c, symmetrize_trace(g.GR, n, g.sT, g.scal + 3, kScal, G, st));
+  pf.launched(HOTRG_ST_GRAM, 4);
+  pf.end(HOTRG_ST_GRAM);
+
+  // ---- a4: FP64 eigendecomposition and choice of U
+  pf.begin(HOTRG_ST_EIG);
+  int spec_n;
+  int eig_path = 0, eig_iters = 0;
+  double eig_res = 0.0;
+  bool fallback = false;
+  if (n <= g.D_cut) {
+    // nothing is cut (U = I); the spectrum of G_L is still recorded
+    CK_CUDA(c, identity_isometry(g.U, n, g.sU, G, st));
+    SiBatch sb{};
+    sb.P = G;
+    sb.n = n;
+    sb.k = n;
+    sb.m = jacobi_block(n);
+    sb.G = pset_linear(g.GL, g.sT);
+    long long nl = 0;
+    CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
+    const SiOut o = si_outputs(c->si_work, G, n, sb.m);
+    CK_CUDA(c, spectrum_no_cut(o.theta, n, 1, g.scal + 2, kScal, rec, g.sRec, spec, g.sSpec, G, st));
+    pf.launched(HOTRG_ST_EIG, 2 + (int)nl);
+    spec_n = n;
+  } else {
+    // leading k = D'+1 eigenpairs of both environments of every instance
+    const int k = Dn + 1;
+    SiBatch sb{};
+    sb.P = 2 * G;
+    sb.n = n;
+    sb.k = k;
+    sb.G = pset_pairs(g.GL, g.GR, g.sT);
+    long long nl = 0;
+    bool ok = false;
+    if (n + (n & 1) <= kSiMaxBlock) {
+      sb.m = jacobi_block(n);
+      CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
+      eig_path = 1;
+      ok = true;
+    } else {
+      int m = ((2 * k + 7) / 8) * 8;
+      if (m > kSiMaxBlock) m = kSiMaxBlock;
+      if (m > n) m = n & ~1;
+      sb.m = m;
+      const int di = ydir ? 1 : 0;
+      if (g.nprev[di] == n && g.kprev[di] <= m) {
+        // the last isometry of this direction starts both sides' iteration
+        sb.warm = pset_pairs(g.Uprev[di], g.Uprev[di], g.sUp);
+        sb.has_warm = true;
+        sb.kw = g.kprev[di];
+      }
+      SiResult r{};
+      CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, 80, st, &r, &nl));
+      eig_path = 2;
+      eig_iters = r.iterations;
+      eig_res = r.residual;
+      ok = r.converged;
+    }
+    pf.launched(HOTRG_ST_EIG, (int)nl);
+    if (ok) {
+      const SiOut o = si_outputs(c->si_work, 2 * G, n, sb.m);
+      SelectArgs a{n, Dn, k, 1, o.theta, o.X, g.scal + 2, kScal, g.U, g.sU,
+                   rec, g.sRec, spec, g.sSpec, G};
+      CK_CUDA(c, select_isometry(a, st));
+    } else {
+      // library fallback, one environment at a time (the own solver leaves
+      // G_L and G_R untouched); vectors overwrite the leading columns of G
+      eig_path = 3;
+      fallback = true;
+      for (int j = 0; j < G; ++j) {
+        if (int r = c->eig.top(g.GL + j * g.sT, n, k, g.wL + j * g.sW, 0))
+          return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (left) failed");
+        if (int r = c->eig.top(g.GR + j * g.sT, n, k, g.wR + j * g.sW, 1))
+          return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (right) failed");
+        int hinfo[2] = {0, 0};
+        CK_CUDA(c, cudaMemcpyAsync(hinfo, c->eig.d_info(), sizeof(hinfo), cudaMemcpyDeviceToHost, st));
+        CK_CUDA(c, cudaStreamSynchronize(st));
+        if (hinfo[0] != 0 || hinfo[1] != 0)
+          return fail(c, HOTRG_EEIG, "eigensolver info = " + std::to_string(hinfo[0]) + ", " +
+                                         std::to_string(hinfo[1]));
+      }
+      SelectArgs a{n, Dn, k, 0, pset_pairs(g.wL, g.wR, g.sW), pset_pairs(g.GL, g.GR, g.sT),
+                   g.scal + 2, kScal, g.U, g.sU, rec, g.sRec, spec, g.sSpec, G};
+      CK_CUDA(c, select_isometry(a, st));
+    }
+    pf.launched(HOTRG_ST_EIG, 1);
+    const int di = ydir ? 1 : 0;
+    CK_CUDA(c, cudaMemcpy2DAsync(g.Uprev[di], sizeof(double) * g.sUp, g.U, sizeof(double) * g.sU,
+                                 sizeof(double) * (size_t)n * Dn, G, cudaMemcpyDeviceToDevice, st));
+    g.nprev[di] = n;
+    g.kprev[di] = Dn;
+    spec_n = k;
+  }
+  (void)fallback;
+  pf.end(HOTRG_ST_EIG);
+
+  // ---- a5-a7: projection chain
+  // output of the step in the stored layout: Y -> T'[a][b][y][y'], X -> T'[x][x'][a][b]
+  const IdxMap tm = ydir ? map3(E, E, 1, E, (long long)Dn * E2)
+                         : map3(E, E, (long long)Dn * Dn, (long long)E * Dn * Dn, Dn);
+  const IdxMap tn = ydir ? map1(E2) : map1(1);
+  if (tc) {
+    if (g.tc.project(g.T, g.sT, g.U, g.sU, D, E, Dn, sx, sxp, sy, syp, g.Tn, g.sT, tm, tn, &pf))
+      return fail(c, HOTRG_ECUDA, "tensor-core projection chain failed");
+  } else {
+    // a5: P[a][x1'][y][x2][k] = sum_x1 U[(x1 x2), a] T[x1,x1',y,k]
+    pf.begin(HOTRG_ST_PROJ_P);
+    MappedGemm g5{(int)(D * Dn), (int)(D * E2), D,
+                  g.U, map2(Dn, n, 1), map1(D),
+                  g.T, map3(E, E, syp, sy, sxp), map1(sx),
+                  g.P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E),
+                  G, g.sU, g.sT, g.sP};
+    CK_CUDA(c, gemm_f64(g5, st));
+    pf.launched(HOTRG_ST_PROJ_P, 1);
+    pf.end(HOTRG_ST_PROJ_P);
+    // a6: Q[a][y][y'][x1'][x2'] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
+    pf.begin(HOTRG_ST_PROJ_Q);
+    MappedGemm g6{(int)(Dn * DE), (int)DE, (int)DE,
+                  g.P, map1(DE), map1(1),
+                  g.T, map2(D, sxp, syp), map2(E, sy, sx),
+                  g.Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2),
+                  G, g.sP, g.sT, g.sP};
+    CK_CUDA(c, gemm_f64(g6, st));
+    pf.launched(HOTRG_ST_PROJ_Q, 1);
+    pf.end(HOTRG_ST_PROJ_Q);
+    // a7: T'[(a,y,y'), b] = sum_{x1',x2'} Q[(a,y,y'),(x1',x2')] U[(x1' x2'), b]
+    pf.begin(HOTRG_ST_PROJ_T);
+    MappedGemm g7{(int)(Dn * E2), Dn, (int)D2,
+                  g.Q, map1(D2), map1(1),
+                  g.U, map1(n), map1(1),
+                  g.Tn, tm, tn,
+                  G, g.sP, g.sU, g.sT};
+    CK_CUDA(c, gemm_f64(g7, st));
+    pf.launched(HOTRG_ST_PROJ_T, 1);
+    pf.end(HOTRG_ST_PROJ_T);
+  }
+
+  // ---- a8: rescale and FP64 log-sum
+  pf.begin(HOTRG_ST_RESCALE);
+  const long long count = (long long)Dn * Dn * E2;
+  CK_CUDA(c, maxabs_scale_log(g.Tn, count, g.sT, g.scal + 1, kScal, g.scal, kScal,
+                              ldexp(1.0, -(step + 1)), rec + 5, g.sRec, c->err, G, st));
+  pf.launched(HOTRG_ST_RESCALE, 3);
+  pf.end(HOTRG_ST_RESCALE);
+  std::swap(g.T, g.Tn);
+  if (ydir) g.dx = Dn; else g.dy = Dn;
+  GroupStep gs{};
+  gs.info.dir = dir;
+  gs.info.Dx = D;
+  gs.info.Dy = E;
+  gs.info.Dn = Dn;
+  gs.info.eig_path = eig_path;
+  gs.info.eig_iters = eig_iters;
+  gs.info.eig_residual = eig_res;
+  gs.spec_count = spec_n;
+  gs.n = n;
+  gs.dn = Dn;
+  g.steps.push_back(gs);
+  return HOTRG_OK;
+}
+
+hotrg_status locate(hotrg_ctx *c, int inst, Group **g, int *j) {
+  if (!c || inst < 0 || inst >= c->n_inst) return HOTRG_EINVAL;
+  *g = c->groups[c->where[inst].first].get();
+  *j = c->where[inst].second;
+  return HOTRG_OK;
+}
+
+hotrg_status step_info_of(hotrg_ctx *c, int inst, int step, hotrg_step_info_t *out) {
+  Group *g;
+  int j;
+  if (!out || locate(c, inst, &g, &j)) return HOTRG_EINVAL;
+  if (c->status != HOTRG_OK) return c->status;
+  if (step < 0 || step >= c->nsteps) return HOTRG_EINVAL;
+  double r[kRecord];
+  CK_CUDA(c, cudaMemcpyAsync(r, g->records + j * g->sRec + (size_t)step * kRecord, sizeof(r),
+                             cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = g->steps[step].info;
+  out->side = (int)r[0];
+  out->eps_L = r[1];
+  out->eps_R = r[2];
+  out->cut_gap = r[3];
+  out->trace_G = r[4];
+  out->ln_c = r[5];
+  return HOTRG_OK;
+}
+
+hotrg_status get_tensor_of(hotrg_ctx *c, int inst, double *host_out, long long cap, int dims[4]) {
+  Group *g;
+  int j;
+  if (!dims || locate(c, inst, &g, &j)) return HOTRG_EINVAL;
+  if (c->status != HOTRG_OK) return c->status;
+  dims[0] = dims[1] = g->dx;
+  dims[2] = dims[3] = g->dy;
+  const long long cnt = (long long)g->dx * g->dx * g->dy * g->dy;
+  if (!host_out || cap < cnt) return HOTRG_EINVAL;
+  CK_CUDA(c, cudaMemcpyAsync(host_out, g->T + j * g->sT, sizeof(double) * cnt,
+                             cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOTRG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -259,68 +661,12 @@ void hotrg_destroy(hotrg_ctx *c) {
 
 hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec, void *stream,
                           hotrg_ctx **out) {
-  if (!out) return HOTRG_EINVAL;
-  *out = nullptr;
-  if (!T0 || D0 < 1 || D0 > 64 || D_cut < 1 || D_cut > 64) return HOTRG_EINVAL;
-  if (prec != HOTRG_FP64 && prec != HOTRG_TF32 && prec != HOTRG_BF16X3 && prec != HOTRG_BF16X6)
-    return HOTRG_EINVAL;
-  hotrg_ctx *c = new (std::nothrow) hotrg_ctx();
-  if (!c) return HOTRG_ENOMEM;
-  auto bail = [&](hotrg_status s) {
-    hotrg_destroy(c);
-    return s;
-  };
-  c->stream = static_cast<cudaStream_t>(stream);
-  c->prof.stream = c->stream;
-  c->D0 = D0;
-  c->D_cut = D_cut;
-  c->Dm = D0 > D_cut ? D0 : D_cut;
-  c->prec = prec;
-  c->dx = c->dy = D0;
-  const long long Dm = c->Dm;
-  const long long t4 = Dm * Dm * Dm * Dm;            // any tensor, partial or Gram matrix
-  const long long p5 = (long long)D_cut * t4;        // P and Q
-  const long long nmax = Dm * Dm;
-  hotrg_status s;
-  if ((s = dalloc(c, &c->T, t4)) || (s = dalloc(c, &c->Tn, t4)) || (s = dalloc(c, &c->AL, t4)) ||
-      (s = dalloc(c, &c->BL, t4)) || (s = dalloc(c, &c->AR, t4)) || (s = dalloc(c, &c->BR, t4)) ||
-      (s = dalloc(c, &c->GL, t4)) || (s = dalloc(c, &c->GR, t4)) || (s = dalloc(c, &c->wL, nmax)) ||
-      (s = dalloc(c, &c->wR, nmax)) || (s = dalloc(c, &c->U, nmax * (D_cut + 1))) ||
-      (s = dalloc(c, &c->scal, 8)) || (s = dalloc(c, &c->err, 4)) ||
-      (s = dalloc(c, &c->records, (size_t)kMaxSteps * kRecord)) ||
-      (s = dalloc(c, &c->spectra, (size_t)kMaxSteps * (D_cut + 1))))
-    return bail(s);
-  {
-    const int nsi = (int)(nmax > kSiMaxBlock + 1 ? nmax : kSiMaxBlock + 1);
-    if ((s = dalloc(c, &c->si_work, (size_t)si_workspace_doubles(2, nsi, kSiMaxBlock))) ||
-        (s = dalloc(c, &c->XL, (size_t)nsi * kSiMaxBlock)) ||
-        (s = dalloc(c, &c->XR, (size_t)nsi * kSiMaxBlock)) || (s = dalloc(c, &c->thL, kSiMaxBlock)) ||
-        (s = dalloc(c, &c->thR, kSiMaxBlock)) || (s = dalloc(c, &c->Uprev[0], nmax * D_cut)) ||
-        (s = dalloc(c, &c->Uprev[1], nmax * D_cut)))
-      return bail(s);
-  }
-  if (prec == HOTRG_FP64) {
-    if ((s = dalloc(c, &c->P, p5)) || (s = dalloc(c, &c->Q, p5))) return bail(s);
-  } else {
-    int r = c->tc.init(prec, D0, D_cut, c->stream, c->err);
-    if (r == 2) return bail(HOTRG_ENOMEM);
-    if (r) return bail(HOTRG_ECUDA);
-  }
-  if (int r = c->eig.init(c->stream)) return bail(r == 2 ? HOTRG_ENOMEM : HOTRG_ECUDA);
-  if (cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess ||
-      cudaMemcpyAsync(c->T, T0, sizeof(double) * D0 * D0 * D0 * D0, cudaMemcpyHostToDevice,
-                      c->stream) != cudaSuccess ||
-      scale_initial(c->T, (long long)D0 * D0 * D0 * D0, c->scal + 1, c->scal, c->err,
-                    c->stream) != cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess)
-    return bail(HOTRG_ECUDA);
-  int herr = 0;
-  if (cudaMemcpy(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return bail(HOTRG_ECUDA);
-  if (herr) return bail(HOTRG_ENONFINITE);
-  *out = c;
-  return HOTRG_OK;
+  return create_ctx(1, &T0, &D0, &D_cut, prec, stream, out);
+}
+
+hotrg_status hotrg_batch_create(int n, const double *const *T0s, const int *D0s, const int *Dcuts,
+                                hotrg_prec prec, void *stream, hotrg_ctx **out) {
+  return create_ctx(n, T0s, D0s, Dcuts, prec, stream, out);
 }
 
 hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
@@ -328,217 +674,22 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   if (c->status != HOTRG_OK) return c->status;
   if (dir != HOTRG_DIR_X && dir != HOTRG_DIR_Y) return HOTRG_EINVAL;
   if (c->nsteps >= kMaxSteps) return fail(c, HOTRG_ESTATE, "step limit reached");
-  cudaStream_t st = c->stream;
-  Profiler &pf = c->prof;
-
-  // ---- the step's view of the stored tensor T[x,x',y,y'] (shape dx,dx,dy,dy)
-  const bool ydir = (dir == HOTRG_DIR_Y);
-  const int D = ydir ? c->dx : c->dy;     // fused legs
-  const int E = ydir ? c->dy : c->dx;     // contracted legs
-  const long long cx = (long long)c->dx * c->dy * c->dy, cxp = (long long)c->dy * c->dy,
-                  cy = c->dy, cyp = 1;
-  const long long sx = ydir ? cx : cy, sxp = ydir ? cxp : cyp;
-  const long long sy = ydir ? cy : cx, syp = ydir ? cyp : cxp;
-  const int n = D * D;
-  const int Dn = n < c->D_cut ? n : c->D_cut;
-  const long long DE = (long long)D * E, E2 = (long long)E * E, D2 = (long long)D * D;
-  const int step = c->nsteps;
-  double *rec = c->records + (size_t)step * kRecord;
-  double *spec = c->spectra + (size_t)step * (c->D_cut + 1);
-  const double fD = D, fE = E, fDn = Dn;
-  pf.flops(HOTRG_ST_ENV, 4.0 * 2.0 * fD * fD * fD * fE * fE * fE);
-  pf.flops(HOTRG_ST_GRAM, 2.0 * 2.0 * fD * fD * fD * fD * fE * fE);
-  pf.flops(HOTRG_ST_PROJ_P, 2.0 * fDn * fD * fD * fD * fE * fE);
-  pf.flops(HOTRG_ST_PROJ_Q, 2.0 * fDn * fD * fD * fD * fE * fE * fE);
-  pf.flops(HOTRG_ST_PROJ_T, 2.0 * fDn * fDn * fD * fD * fE * fE);
-
-  // ---- a2/a3: environments G_L, G_R ([x1][x2][u1][u2], FP64)
-  const bool tc = (c->prec != HOTRG_FP64);
-  if (tc) {
-    if (c->tc.environment(c->T, D, E, sx, sxp, sy, syp, c->GL, c->GR, &pf))
-      return fail(c, HOTRG_ECUDA, "tensor-core environment chain failed");
-  } else {
-    // partials written as [x][u][k][k'] for the Gram combine
-    const IdxMap out_m = map2(E, E, (long long)D * E2), out_n = map2(E, 1, E2);
-    struct Part { double *dst; IdxMap row, red; };
-    const Part parts[4] = {
-        {c->AL, map2(E, syp, sx), map2(E, sy, sxp)},    // A_L[x1,k,u1,k']: sum over (x1', y)
-        {c->BL, map2(E, sy, sx), map2(E, syp, sxp)},    // B_L[x2,k,u2,k']: sum over (x2', y')
-        {c->AR, map2(E, syp, sxp), map2(E, sy, sx)},    // A_R[x1',k,u1',k']: sum over (x1, y)
-        {c->BR, map2(E, sy, sxp), map2(E, syp, sx)},    // B_R[x2',k,u2',k']: sum over (x2, y')
-    };
-    pf.begin(HOTRG_ST_ENV);
-    for (const Part &p : parts) {
-      MappedGemm g{(int)DE, (int)DE, (int)DE, c->T, p.row, p.red, c->T, p.row, p.red, p.dst, out_m, out_n};
-      CK_CUDA(c, gemm_f64(g, st));
-    }
-    pf.launched(HOTRG_ST_ENV, 4);
-    pf.end(HOTRG_ST_ENV);
-    // G[x1,x2,u1,u2] = sum_{k,k'} A[x1,u1,k,k'] B[x2,u2,k,k']
-    pf.begin(HOTRG_ST_GRAM);
-    const IdxMap gm = map2(D, D, D2 * D), gn = map2(D, 1, D2);
-    MappedGemm gl{(int)D2, (int)D2, (int)E2, c->AL, map1(E2), map1(1), c->BL, map1(E2), map1(1), c->GL, gm, gn};
-    MappedGemm gr{(int)D2, (int)D2, (int)E2, c->AR, map1(E2), map1(1), c->BR, map1(E2), map1(1), c->GR, gm, gn};
-    CK_CUDA(c, gemm_f64(gl, st));
-    CK_CUDA(c, gemm_f64(gr, st));
-    pf.launched(HOTRG_ST_GRAM, 2);
-  }
-  CK_CUDA(c, symmetrize_trace(c->GL, n, c->scal + 2, st));
-  CK_CUDA(c, symmetrize_trace(c->GR, n, c->scal + 3, st));
-  pf.launched(HOTRG_ST_GRAM, 4);
-  pf.end(HOTRG_ST_GRAM);
-
-  // ---- a4: FP64 eigendecomposition and choice of U
-  pf.begin(HOTRG_ST_EIG);
-  int spec_n;
-  int eig_path = 0, eig_iters = 0;
-  double eig_res = 0.0;
-  if (n <= c->D_cut) {
-    // nothing is cut (U = I); the spectrum of G_L is still recorded
-    CK_CUDA(c, identity_isometry(c->U, n, st));
-    SiBatch sb{};
-    sb.P = 1;
-    sb.n = n;
-    sb.k = n;
-    sb.G[0] = c->GL;
-    sb.X[0] = c->XL;
-    sb.theta[0] = c->thL;
-    long long nl = 0;
-    CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
-    CK_CUDA(c, spectrum_no_cut(c->thL, n, 1, c->scal + 2, rec, spec, st));
-    pf.launched(HOTRG_ST_EIG, 2 + (int)nl);
-    spec_n = n;
-  } else {
-    // leading k = D'+1 eigenpairs of both environments (batched FP64 solver)
-    const int k = Dn + 1;
-    SiBatch sb{};
-    sb.P = 2;
-    sb.n = n;
-    sb.k = k;
-    sb.G[0] = c->GL;
-    sb.G[1] = c->GR;
-    sb.X[0] = c->XL;
-    sb.X[1] = c->XR;
-    sb.theta[0] = c->thL;
-    sb.theta[1] = c->thR;
-    long long nl = 0;
-    bool ok = false;
-    if (n + (n & 1) <= kSiMaxBlock) {
-      CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
-      eig_path = 1;
-      ok = true;
-    } else {
-      int m = ((2 * k + 7) / 8) * 8;
-      if (m > kSiMaxBlock) m = kSiMaxBlock;
-      if (m > n) m = n & ~1;
-      sb.m = m;
-      const int di = ydir ? 1 : 0;
-      if (c->nprev[di] == n && c->kprev[di] <= m) {
-        sb.warm[0] = sb.warm[1] = c->Uprev[di];
-        sb.kw = c->kprev[di];
-      }
-      SiResult r{};
-      CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, 80, st, &r, &nl));
-      eig_path = 2;
-      eig_iters = r.iterations;
-      eig_res = r.residual;
-      ok = r.converged;
-    }
-    pf.launched(HOTRG_ST_EIG, (int)nl);
-    if (ok) {
-      SelectArgs a{n, Dn, k, 1, c->thL, c->thR, c->XL, c->XR, c->scal + 2, c->scal + 3, c->U, rec, spec};
-      CK_CUDA(c, select_isometry(a, st));
-    } else {
-      // library fallback (G_L, G_R are untouched by the own solver)
-      eig_path = 3;
-      if (int r = c->eig.top(c->GL, n, k, c->wL, 0))
-        return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (left) failed");
-      if (int r = c->eig.top(c->GR, n, k, c->wR, 1))
-        return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (right) failed");
-      SelectArgs a{n, Dn, k, 0, c->wL, c->wR, c->GL, c->GR, c->scal + 2, c->scal + 3, c->U, rec, spec};
-      CK_CUDA(c, select_isometry(a, st));
-    }
-    pf.launched(HOTRG_ST_EIG, 1);
-    const int di = ydir ? 1 : 0;
-    CK_CUDA(c, cudaMemcpyAsync(c->Uprev[di], c->U, sizeof(double) * (size_t)n * Dn,
-                               cudaMemcpyDeviceToDevice, st));
-    c->nprev[di] = n;
-    c->kprev[di] = Dn;
-    spec_n = k;
-  }
-  pf.end(HOTRG_ST_EIG);
-  int hinfo[2] = {0, 0};
-  CK_CUDA(c, cudaMemcpyAsync(hinfo, c->eig.d_info(), sizeof(hinfo), cudaMemcpyDeviceToHost, st));
-  CK_CUDA(c, cudaStreamSynchronize(st));
-  pf.collect(false);
+  for (auto &g : c->groups)
+    if (hotrg_status s = step_group(c, *g, dir, c->nsteps)) return s;
+  // one synchronisation per step: device errors of this step surface here
+  CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->prof.collect(false);
   if (hotrg_status fs = check_flag(c)) return fs;
-  if (eig_path == 3 && (hinfo[0] != 0 || hinfo[1] != 0))
-    return fail(c, HOTRG_EEIG, "eigensolver info = " + std::to_string(hinfo[0]) + ", " +
-                                   std::to_string(hinfo[1]));
+  if (c->prof.on) c->prof.acc.steps += 1;
+  c->nsteps += 1;
+  return HOTRG_OK;
+}
 
-  // ---- a5-a7: projection chain
-  // output of the step in the stored layout: Y -> T'[a][b][y][y'], X -> T'[x][x'][a][b]
-  const IdxMap tm = ydir ? map3(E, E, 1, E, (long long)Dn * E2)
-                         : map3(E, E, (long long)Dn * Dn, (long long)E * Dn * Dn, Dn);
-  const IdxMap tn = ydir ? map1(E2) : map1(1);
-  if (tc) {
-    if (c->tc.project(c->T, c->U, D, E, Dn, sx, sxp, sy, syp, c->Tn, tm, tn, &pf))
-      return fail(c, HOTRG_ECUDA, "tensor-core projection chain failed");
-  } else {
-    // a5: P[a][x1'][y][x2][k] = sum_x1 U[(x1 x2), a] T[x1,x1',y,k]
-    pf.begin(HOTRG_ST_PROJ_P);
-    MappedGemm g5{(int)(D * Dn), (int)(D * E2), D,
-                  c->U, map2(Dn, n, 1), map1(D),
-                  c->T, map3(E, E, syp, sy, sxp), map1(sx),
-                  c->P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E)};
-    CK_CUDA(c, gemm_f64(g5, st));
-    pf.launched(HOTRG_ST_PROJ_P, 1);
-    pf.end(HOTRG_ST_PROJ_P);
-    // a6: Q[a][y][y'][x1'][x2'] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
-    pf.begin(HOTRG_ST_PROJ_Q);
-    MappedGemm g6{(int)(Dn * DE), (int)DE, (int)DE,
-                  c->P, map1(DE), map1(1),
-                  c->T, map2(D, sxp, syp), map2(E, sy, sx),
-                  c->Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2)};
-    CK_CUDA(c, gemm_f64(g6, st));
-    pf.launched(HOTRG_ST_PROJ_Q, 1);
-    pf.end(HOTRG_ST_PROJ_Q);
-    // a7: T'[(a,y,y'), b] = sum_{x1',x2'} Q[(a,y,y'),(x1',x2')] U[(x1' x2'), b]
-    pf.begin(HOTRG_ST_PROJ_T);
-    MappedGemm g7{(int)(Dn * E2), Dn, (int)D2,
-                  c->Q, map1(D2), map1(1),
-                  c->U, map1(n), map1(1),
-                  c->Tn, tm, tn};
-    CK_CUDA(c, gemm_f64(g7, st));
-    pf.launched(HOTRG_ST_PROJ_T, 1);
-    pf.end(HOTRG_ST_PROJ_T);
-  }
+hotrg_status hotrg_batch_step(hotrg_ctx *c, hotrg_dir dir) { return hotrg_step(c, dir); }
 
-  // ---- a8: rescale and FP64 log-sum
-  pf.begin(HOTRG_ST_RESCALE);
-  const long long count = (long long)Dn * Dn * E2;
-  CK_CUDA(c, maxabs_scale_log(c->Tn, count, c->scal + 1, c->scal, ldexp(1.0, -(step + 1)),
-                              rec + 5, c->err, st));
-  pf.launched(HOTRG_ST_RESCALE, 2);
-  pf.end(HOTRG_ST_RESCALE);
-  if (pf.on) pf.acc.steps += 1;
-  double *tmp = c->T;
-  c->T = c->Tn;
-  c->Tn = tmp;
-  if (ydir) c->dx = Dn; else c->dy = Dn;
-  c->last_n = n;
-  c->last_dn = Dn;
-  c->nsteps = step + 1;
-  hotrg_step_info_t inf{};
-  inf.dir = dir;
-  inf.Dx = D;
-  inf.Dy = E;
-  inf.Dn = Dn;
-  inf.eig_path = eig_path;
-  inf.eig_iters = eig_iters;
-  inf.eig_residual = eig_res;
-  c->info.push_back(inf);
-  c->spec_count.push_back(spec_n);
+hotrg_status hotrg_batch_size(hotrg_ctx *c, int *n) {
+  if (!c || !n) return HOTRG_EINVAL;
+  *n = c->n_inst;
   return HOTRG_OK;
 }
 
@@ -560,18 +711,34 @@ hotrg_status hotrg_profile_read(hotrg_ctx *c, hotrg_profile_t *out) {
   return HOTRG_OK;
 }
 
-hotrg_status hotrg_log_z_per_site(hotrg_ctx *c, double *out) {
-  if (!c || !out) return HOTRG_EINVAL;
+hotrg_status hotrg_batch_log_z(hotrg_ctx *c, double *out_n) {
+  if (!c || !out_n) return HOTRG_EINVAL;
   if (c->status != HOTRG_OK) return c->status;
-  CK_CUDA(c, periodic_trace(c->T, c->dx, c->dy, c->scal + 4, c->stream));
-  double h[5];
-  CK_CUDA(c, cudaMemcpyAsync(h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<std::vector<double>> h(c->groups.size());
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    Group &g = *c->groups[gi];
+    CK_CUDA(c, periodic_trace(g.T, g.dx, g.dy, g.sT, g.scal + 4, kScal, g.G, c->stream));
+    h[gi].resize((size_t)kScal * g.G);
+    CK_CUDA(c, cudaMemcpyAsync(h[gi].data(), g.scal, sizeof(double) * kScal * g.G,
+                               cudaMemcpyDeviceToHost, c->stream));
+  }
   CK_CUDA(c, cudaStreamSynchronize(c->stream));
   if (hotrg_status fs = check_flag(c)) return fs;
-  if (!(h[4] > 0.0) || !isfinite(h[4]))
-    return fail(c, HOTRG_ENONFINITE, "periodic trace is not positive");
-  *out = h[0] + log(h[4]) * ldexp(1.0, -c->nsteps);
+  const double w = ldexp(1.0, -c->nsteps);
+  for (int i = 0; i < c->n_inst; ++i) {
+    const double *s = h[c->where[i].first].data() + (size_t)kScal * c->where[i].second;
+    if (!(s[4] > 0.0) || !isfinite(s[4]))
+      return fail(c, HOTRG_ENONFINITE,
+                  "periodic trace of instance " + std::to_string(i) + " is not positive");
+    out_n[i] = s[0] + log(s[4]) * w;
+  }
   return HOTRG_OK;
+}
+
+hotrg_status hotrg_log_z_per_site(hotrg_ctx *c, double *out) {
+  if (!c || !out) return HOTRG_EINVAL;
+  if (c->n_inst != 1) return HOTRG_ESTATE;
+  return hotrg_batch_log_z(c, out);
 }
 
 hotrg_status hotrg_free_energy(hotrg_ctx *c, double beta, double *f_out) {
@@ -584,67 +751,60 @@ hotrg_status hotrg_free_energy(hotrg_ctx *c, double beta, double *f_out) {
 }
 
 hotrg_status hotrg_step_info(hotrg_ctx *c, int step, hotrg_step_info_t *out) {
-  if (!c || !out) return HOTRG_EINVAL;
-  if (c->status != HOTRG_OK) return c->status;
-  if (step < 0 || step >= c->nsteps) return HOTRG_EINVAL;
-  double r[kRecord];
-  CK_CUDA(c, cudaMemcpyAsync(r, c->records + (size_t)step * kRecord, sizeof(r),
-                             cudaMemcpyDeviceToHost, c->stream));
-  CK_CUDA(c, cudaStreamSynchronize(c->stream));
-  *out = c->info[step];
-  out->side = (int)r[0];
-  out->eps_L = r[1];
-  out->eps_R = r[2];
-  out->cut_gap = r[3];
-  out->trace_G = r[4];
-  out->ln_c = r[5];
-  return HOTRG_OK;
+  return step_info_of(c, 0, step, out);
+}
+
+hotrg_status hotrg_batch_step_info(hotrg_ctx *c, int inst, int step, hotrg_step_info_t *out) {
+  return step_info_of(c, inst, step, out);
 }
 
 hotrg_status hotrg_spectrum(hotrg_ctx *c, int step, double *buf, int cap, int *n) {
   if (!c || !n || (cap > 0 && !buf)) return HOTRG_EINVAL;
   if (c->status != HOTRG_OK) return c->status;
   if (step < 0 || step >= c->nsteps) return HOTRG_EINVAL;
-  const int cnt = c->spec_count[step];
+  const Group &g = *c->groups[c->where[0].first];
+  const int j = c->where[0].second;
+  const int cnt = g.steps[step].spec_count;
   *n = cnt;
   const int k = cnt < cap ? cnt : cap;
   if (k > 0) {
-    CK_CUDA(c, cudaMemcpyAsync(buf, c->spectra + (size_t)step * (c->D_cut + 1), sizeof(double) * k,
-                               cudaMemcpyDeviceToHost, c->stream));
+    CK_CUDA(c, cudaMemcpyAsync(buf, g.spectra + j * g.sSpec + (size_t)step * (g.D_cut + 1),
+                               sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
     CK_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   return HOTRG_OK;
 }
 
 hotrg_status hotrg_get_tensor(hotrg_ctx *c, double *host_out, long long cap, int dims[4]) {
-  if (!c || !dims) return HOTRG_EINVAL;
-  if (c->status != HOTRG_OK) return c->status;
-  dims[0] = dims[1] = c->dx;
-  dims[2] = dims[3] = c->dy;
-  const long long cnt = (long long)c->dx * c->dx * c->dy * c->dy;
-  if (!host_out || cap < cnt) return HOTRG_EINVAL;
-  CK_CUDA(c, cudaMemcpyAsync(host_out, c->T, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
-  CK_CUDA(c, cudaStreamSynchronize(c->stream));
-  return HOTRG_OK;
+  return get_tensor_of(c, 0, host_out, cap, dims);
+}
+
+hotrg_status hotrg_batch_get_tensor(hotrg_ctx *c, int inst, double *host_out, long long cap,
+                                    int dims[4]) {
+  return get_tensor_of(c, inst, host_out, cap, dims);
 }
 
 hotrg_status hotrg_get_isometry(hotrg_ctx *c, double *host_out, long long cap, int *rows, int *cols) {
   if (!c || !rows || !cols) return HOTRG_EINVAL;
   if (c->status != HOTRG_OK) return c->status;
   if (c->nsteps == 0) return HOTRG_ESTATE;
-  *rows = c->last_n;
-  *cols = c->last_dn;
-  const long long cnt = (long long)c->last_n * c->last_dn;
+  const Group &g = *c->groups[c->where[0].first];
+  const int j = c->where[0].second;
+  *rows = g.steps.back().n;
+  *cols = g.steps.back().dn;
+  const long long cnt = (long long)*rows * *cols;
   if (!host_out || cap < cnt) return HOTRG_EINVAL;
-  CK_CUDA(c, cudaMemcpyAsync(host_out, c->U, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CK_CUDA(c, cudaMemcpyAsync(host_out, g.U + j * g.sU, sizeof(double) * cnt,
+                             cudaMemcpyDeviceToHost, c->stream));
   CK_CUDA(c, cudaStreamSynchronize(c->stream));
   return HOTRG_OK;
 }
 
 hotrg_status hotrg_dims(hotrg_ctx *c, int *Dx, int *Dy, int *nsteps) {
   if (!c || !Dx || !Dy || !nsteps) return HOTRG_EINVAL;
-  *Dx = c->dx;
-  *Dy = c->dy;
+  const Group &g = *c->groups[c->where[0].first];
+  *Dx = g.dx;
+  *Dy = g.dy;
   *nsteps = c->nsteps;
   return HOTRG_OK;
 }

@@ -58,12 +58,12 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return true;
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int c0, int c1, int c2) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
 
@@ -214,8 +214,10 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // N tiles run fastest: the CTAs that share an A tile are launched together and
-  // read it from L2 instead of HBM
+  // read it from L2 instead of HBM; grid.z is the instance of the batch
   const int m0 = blockIdx.y * C::BM, n0 = blockIdx.x * BN;
+  epi.C = static_cast<char *>(epi.C) +
+          blockIdx.z * epi.bstride * (epi.kind == OutKind::F64 ? 8 : (epi.kind == OutKind::F32 ? 4 : 2));
   const int nkb = (K + Tr::kBK - 1) / Tr::kBK;
 
   auto a_tile = [&](int s, int p) { return smem_base + s * C::STAGE_BYTES + p * C::A_BYTES; };
@@ -259,8 +261,10 @@ __global__ void __launch_bounds__(128, 1)
       }
       const uint32_t fb = smem_u32(&full_bar[s]);
       mbar_expect_tx(fb, C::STAGE_BYTES);
-      for (int p = 0; p < Tr::kPlanes; ++p) tma_load_3d(a_tile(s, p), &ta, fb, kb * Tr::kBK, m0, p);
-      for (int p = 0; p < Tr::kPlanes; ++p) tma_load_3d(b_tile(s, p), &tb, fb, kb * Tr::kBK, n0, p);
+      for (int p = 0; p < Tr::kPlanes; ++p)
+        tma_load_4d(a_tile(s, p), &ta, fb, kb * Tr::kBK, m0, p, blockIdx.z);
+      for (int p = 0; p < Tr::kPlanes; ++p)
+        tma_load_4d(b_tile(s, p), &tb, fb, kb * Tr::kBK, n0, p, blockIdx.z);
     }
     s_issued = kb;
   } else if (warp == 1 && lane == 0) {
@@ -369,20 +373,23 @@ bool make_map(CUtensorMap *m, TcMode mode, const TcOperand &op, int box_rows) {
   if (!enc) return false;
   const int eb = tc_elem_bytes(mode);
   const int planes = tc_planes(mode);
-  cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)op.pitch * eb, (cuuint64_t)op.pitch * eb * op.rows};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
+  const long long bs = op.batch > 1 ? op.bstride : (long long)op.pitch * op.rows * planes;
+  cuuint64_t dims[4] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)planes,
+                        (cuuint64_t)(op.batch < 1 ? 1 : op.batch)};
+  cuuint64_t strides[3] = {(cuuint64_t)op.pitch * eb, (cuuint64_t)op.pitch * eb * op.rows,
+                           (cuuint64_t)bs * eb};
+  cuuint32_t box[4] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       mode == TcMode::TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  CUresult r = enc(m, dt, 3, const_cast<void *>(op.base), dims, strides, box, estr,
+  CUresult r = enc(m, dt, 4, const_cast<void *>(op.base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 template <int MODE, int BN>
-cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K,
+cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int batch,
                    const TcEpilogue &epi, int *err, cudaStream_t s) {
   using C = Cfg<MODE, BN>;
   static bool attr_set = false;
@@ -392,8 +399,8 @@ cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, i
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((N + BN - 1) / BN, (M + C::BM - 1) / C::BM);
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  dim3 grid((N + BN - 1) / BN, (M + C::BM - 1) / C::BM, batch);
+  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
   k_tc_gemm<MODE, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, epi, err);
   return cudaGetLastError();
 }
@@ -405,9 +412,10 @@ cudaError_t dispatch_bn(const TcOperand &A, const TcOperand &B, int M, int N, in
   const int bn = N <= 64 ? 64 : (N <= 128 || MODE != 0 ? 128 : 256);
   CUtensorMap ta, tb;
   if (!make_map(&ta, mode, A, 128) || !make_map(&tb, mode, B, bn)) return cudaErrorInvalidValue;
-  if (bn == 64) return launch<MODE, 64>(ta, tb, M, N, K, epi, err, s);
-  if (bn == 128) return launch<MODE, 128>(ta, tb, M, N, K, epi, err, s);
-  if constexpr (MODE == 0) return launch<MODE, 256>(ta, tb, M, N, K, epi, err, s);
+  const int batch = A.batch < 1 ? 1 : A.batch;
+  if (bn == 64) return launch<MODE, 64>(ta, tb, M, N, K, batch, epi, err, s);
+  if (bn == 128) return launch<MODE, 128>(ta, tb, M, N, K, batch, epi, err, s);
+  if constexpr (MODE == 0) return launch<MODE, 256>(ta, tb, M, N, K, batch, epi, err, s);
   return cudaErrorInvalidValue;
 }
 
@@ -417,6 +425,13 @@ cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, 
                     const TcEpilogue &epi, int *err_flag, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K <= 0 || A.K != K || B.K != K || A.rows < M || B.rows < N) return cudaErrorInvalidValue;
+  if ((A.batch < 1 ? 1 : A.batch) != (B.batch < 1 ? 1 : B.batch)) return cudaErrorInvalidValue;
+  {
+    // TMA strides must be multiples of 16 bytes
+    const int eb = tc_elem_bytes(mode);
+    if ((A.batch > 1 && (A.bstride * eb) % 16) || (B.batch > 1 && (B.bstride * eb) % 16))
+      return cudaErrorInvalidValue;
+  }
   if (A.pitch != tc_pitch(A.pitch, mode) || B.pitch != tc_pitch(B.pitch, mode) || A.pitch < K ||
       B.pitch < K)
     return cudaErrorInvalidValue;

@@ -25,11 +25,14 @@ inline int tc_elem_bytes(TcMode m) { return m == TcMode::TF32 ? 4 : 2; }
 enum class OutKind : int { F32 = 0, F64 = 1, BF16P = 2 };
 
 // A dense operand in global memory: `planes` planes of `rows` x `pitch`
-// elements (K contiguous), plane stride rows * pitch.  Only the first K
-// columns are read (the rest of each row is padding).
+// elements (K contiguous), plane stride rows * pitch, for `batch` instances
+// `bstride` elements apart.  Only the first K columns are read (the rest of
+// each row is padding).
 struct TcOperand {
   const void *base;
   int rows, K, pitch;
+  int batch;
+  long long bstride;
 };
 
 struct TcEpilogue {
@@ -39,12 +42,14 @@ struct TcEpilogue {
   int planes;              // output planes (BF16P): 1, 2 or 3
   bool round_tf32;         // F32 output feeds a TF32 operand: round to nearest TF32
   IdxMap cm, cn;
+  long long bstride;       // elements between the outputs of consecutive instances
   bool transpose;          // set by tc_gemm: stage through shared memory so that a warp
                            // stores 32 consecutive columns of one row (unit-stride cn)
 };
 
-// Launches one GEMM C(M x N) = A(M x K) . B(N x K)^T; returns a CUDA error
-// code (cudaErrorInvalidValue for unsupported shapes).
+// Launches C(M x N) = A(M x K) . B(N x K)^T for every instance of the batch
+// (A.batch == B.batch; grid.z runs over instances); returns a CUDA error code
+// (cudaErrorInvalidValue for unsupported shapes).
 cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, int N, int K,
                     const TcEpilogue &epi, int *err_flag, cudaStream_t s);
 

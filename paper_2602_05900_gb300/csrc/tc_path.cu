@@ -18,6 +18,8 @@ struct TcPath::Impl {
   TcMode mode = TcMode::TF32;
   cudaStream_t s = nullptr;
   int planes = 1, eb = 4;
+  int G = 1;                       // instances
+  long long sTop = 0, sPop = 0;    // elements between instances: operand buffers, P / Q
   void *opT[4] = {};       // a2 operands: permuted views of T
   void *part[4] = {};      // a2 outputs / a3 operands: [x][u] x [k][k']
   void *opU5 = nullptr, *opT5 = nullptr, *opT6 = nullptr, *opU7 = nullptr;
@@ -46,8 +48,10 @@ __device__ __forceinline__ float tf32_rna(float v) {
 
 // dst[p][r][k] (pitch columns, zero beyond K) = split_p(src[rm(r) + km(k)])
 template <int MODE>
-__global__ void k_gather(const double *src, int R, int K, int pitch, IdxMap rm, IdxMap km,
-                         void *dst, long long plane_stride) {
+__global__ void k_gather(const double *src, long long sSrc, int R, int K, int pitch, IdxMap rm,
+                         IdxMap km, void *dst, long long sDst, long long plane_stride) {
+  src += blockIdx.y * sSrc;
+  dst = static_cast<char *>(dst) + blockIdx.y * sDst * (MODE == 0 ? 4 : 2);
   const long long total = (long long)R * pitch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -69,9 +73,10 @@ __global__ void k_gather(const double *src, int R, int K, int pitch, IdxMap rm, 
   }
 }
 
-int grid_for(long long count) {
+int grid_for(long long count, int batch) {
   long long b = (count + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  const long long cap = (152LL * 8 + batch - 1) / batch;
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -88,11 +93,12 @@ void *alloc(std::size_t bytes) {
 
 TcPath::~TcPath() { delete impl_; }
 
-int TcPath::init(hotrg_prec prec, int D0, int D_cut, cudaStream_t s, int *err_flag) {
+int TcPath::init(hotrg_prec prec, int D0, int D_cut, int G, cudaStream_t s, int *err_flag) {
   impl_ = new Impl();
   Impl &I = *impl_;
   I.mode = prec == HOTRG_TF32 ? TcMode::TF32 : (prec == HOTRG_BF16X3 ? TcMode::BF16X3 : TcMode::BF16X6);
   I.s = s;
+  I.G = G;
   I.planes = tc_planes(I.mode);
   I.eb = tc_elem_bytes(I.mode);
   const long long Dm = D0 > D_cut ? D0 : D_cut;
@@ -101,7 +107,10 @@ int TcPath::init(hotrg_prec prec, int D0, int D_cut, cudaStream_t s, int *err_fl
   // <= Dm^3 (Dm + 8) elements, and every D^5 intermediate fits D_cut Dm^2 (Dm^2 + 8).
   I.capT = (std::size_t)(Dm * Dm * Dm * (Dm + 8));
   I.capP = (std::size_t)(D_cut * Dm * Dm * (Dm * Dm + 8));
-  const std::size_t bt = I.capT * I.planes * I.eb, bp = I.capP * I.planes * I.eb;
+  // instance strides: all planes of an instance, rounded to 64 elements (TMA strides)
+  I.sTop = ((long long)I.capT * I.planes + 63) / 64 * 64;
+  I.sPop = ((long long)I.capP * I.planes + 63) / 64 * 64;
+  const std::size_t bt = (std::size_t)I.sTop * G * I.eb, bp = (std::size_t)I.sPop * G * I.eb;
   for (int i = 0; i < 4; ++i) {
     if (!(I.opT[i] = alloc(bt))) return 2;
     if (!(I.part[i] = alloc(bt))) return 2;
@@ -113,21 +122,26 @@ int TcPath::init(hotrg_prec prec, int D0, int D_cut, cudaStream_t s, int *err_fl
   return 0;
 }
 
-static cudaError_t gather(const TcPath::Impl &I, const double *src, int R, int K, int pitch,
-                          IdxMap rm, IdxMap km, void *dst) {
+static cudaError_t gather(const TcPath::Impl &I, const double *src, long long sSrc, int R, int K,
+                          int pitch, IdxMap rm, IdxMap km, void *dst) {
   const long long ps = (long long)R * pitch;
-  const int g = grid_for(ps);
+  const dim3 g(grid_for(ps, I.G), I.G);
   switch (I.mode) {
-    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, R, K, pitch, rm, km, dst, ps); break;
-    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, R, K, pitch, rm, km, dst, ps); break;
-    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, R, K, pitch, rm, km, dst, ps); break;
+    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps); break;
+    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps); break;
+    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps); break;
   }
   return cudaGetLastError();
 }
 
+static TcOperand operand(const TcPath::Impl &I, const void *base, int rows, int K, int pitch,
+                         long long bstride) {
+  return TcOperand{base, rows, K, pitch, I.G, bstride};
+}
+
 // Epilogue writing an operand-format result (next GEMM's A or B planes).
 static TcEpilogue operand_epilogue(const TcPath::Impl &I, void *dst, long long plane_stride,
-                                   IdxMap cm, IdxMap cn) {
+                                   IdxMap cm, IdxMap cn, long long bstride) {
   TcEpilogue e{};
   if (I.mode == TcMode::TF32) {
     e.kind = OutKind::F32;
@@ -140,21 +154,24 @@ static TcEpilogue operand_epilogue(const TcPath::Impl &I, void *dst, long long p
   e.plane_stride = plane_stride;
   e.cm = cm;
   e.cn = cn;
+  e.bstride = bstride;
   return e;
 }
 
-static TcEpilogue f64_epilogue(double *dst, IdxMap cm, IdxMap cn) {
+static TcEpilogue f64_epilogue(double *dst, IdxMap cm, IdxMap cn, long long bstride) {
   TcEpilogue e{};
   e.kind = OutKind::F64;
   e.C = dst;
   e.planes = 1;
   e.cm = cm;
   e.cn = cn;
+  e.bstride = bstride;
   return e;
 }
 
-int TcPath::environment(const double *T, int D, int E, long long sx, long long sxp, long long sy,
-                        long long syp, double *GL, double *GR, StageHook *hook) {
+int TcPath::environment(const double *T, long long sT, int D, int E, long long sx, long long sxp,
+                        long long sy, long long syp, double *GL, double *GR, long long sG,
+                        StageHook *hook) {
   Impl &I = *impl_;
   const int DE = D * E, E2 = E * E, D2 = D * D;
   const int p2 = tc_pitch(DE, I.mode);   // a2 operand pitch
@@ -164,15 +181,15 @@ int TcPath::environment(const double *T, int D, int E, long long sx, long long s
   const IdxMap reds[4] = {map2(E, sy, sxp), map2(E, syp, sxp), map2(E, sy, sx), map2(E, syp, sx)};
   hook->begin(HOTRG_ST_PREP);
   for (int i = 0; i < 4; ++i)
-    if (gather(I, T, DE, DE, p2, rows[i], reds[i], I.opT[i]) != cudaSuccess) return 1;
+    if (gather(I, T, sT, DE, DE, p2, rows[i], reds[i], I.opT[i]) != cudaSuccess) return 1;
   hook->launched(HOTRG_ST_PREP, 4);
   hook->end(HOTRG_ST_PREP);
   hook->begin(HOTRG_ST_ENV);
   for (int i = 0; i < 4; ++i) {
     // part[i][(x,u)][(k,k')]: rows m = (x, k), cols n = (u, k')
-    TcOperand op{I.opT[i], DE, DE, p2};
+    TcOperand op = operand(I, I.opT[i], DE, DE, p2, I.sTop);
     TcEpilogue ep = operand_epilogue(I, I.part[i], (long long)D2 * p3,
-                                     map2(E, E, (long long)D * p3), map2(E, 1, p3));
+                                     map2(E, E, (long long)D * p3), map2(E, 1, p3), I.sTop);
     if (tc_gemm(I.mode, op, op, DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
   }
   hook->launched(HOTRG_ST_ENV, 4);
@@ -180,9 +197,9 @@ int TcPath::environment(const double *T, int D, int E, long long sx, long long s
   hook->begin(HOTRG_ST_GRAM);
   const IdxMap gm = map2(D, D, (long long)D2 * D), gn = map2(D, 1, D2);
   for (int side = 0; side < 2; ++side) {
-    TcOperand a{I.part[2 * side], D2, E2, p3};
-    TcOperand b{I.part[2 * side + 1], D2, E2, p3};
-    if (tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(side ? GR : GL, gm, gn), I.err, I.s) !=
+    TcOperand a = operand(I, I.part[2 * side], D2, E2, p3, I.sTop);
+    TcOperand b = operand(I, I.part[2 * side + 1], D2, E2, p3, I.sTop);
+    if (tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(side ? GR : GL, gm, gn, sG), I.err, I.s) !=
         cudaSuccess)
       return 1;
   }
@@ -190,9 +207,9 @@ int TcPath::environment(const double *T, int D, int E, long long sx, long long s
   return 0;   // the driver closes the GRAM stage after symmetrising
 }
 
-int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long long sx,
-                    long long sxp, long long sy, long long syp, double *Tout, IdxMap tm,
-                    IdxMap tn, StageHook *hook) {
+int TcPath::project(const double *T, long long sT, const double *U, long long sU, int D, int E,
+                    int Dn, long long sx, long long sxp, long long sy, long long syp, double *Tout,
+                    long long sTout, IdxMap tm, IdxMap tn, StageHook *hook) {
   Impl &I = *impl_;
   const int n = D * D, DE = D * E, E2 = E * E;
   const int p5 = tc_pitch(D, I.mode), p6 = tc_pitch(DE, I.mode), p7 = tc_pitch(n, I.mode);
@@ -202,22 +219,22 @@ int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long
     return 1;
   // a1: operands of a5 (U and T views with the x1 axis as K), a6 (T view) and a7 (U^T)
   hook->begin(HOTRG_ST_PREP);
-  if (gather(I, U, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5) != cudaSuccess) return 1;
-  if (gather(I, T, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5) != cudaSuccess)
+  if (gather(I, U, sU, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5) != cudaSuccess) return 1;
+  if (gather(I, T, sT, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5) != cudaSuccess)
     return 1;
-  if (gather(I, T, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6) != cudaSuccess)
+  if (gather(I, T, sT, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6) != cudaSuccess)
     return 1;
-  if (gather(I, U, Dn, n, p7, map1(n), map1(1), I.opU7) != cudaSuccess) return 1;
+  if (gather(I, U, sU, Dn, n, p7, map1(n), map1(1), I.opU7) != cudaSuccess) return 1;
   hook->launched(HOTRG_ST_PREP, 4);
   hook->end(HOTRG_ST_PREP);
 
   // a5: P[(a,x1',y)][(x2,k)] = sum_x1 U[(x1 x2),a] T[x1,x1',y,k]; rows m = (x2,a), cols (x1',y,k)
   hook->begin(HOTRG_ST_PROJ_P);
   {
-    TcOperand a{I.opU5, D * Dn, D, p5}, b{I.opT5, D * E2, D, p5};
+    TcOperand a = operand(I, I.opU5, D * Dn, D, p5, I.sTop), b = operand(I, I.opT5, D * E2, D, p5, I.sTop);
     const long long ps = (long long)Dn * DE * p6;
     TcEpilogue ep = operand_epilogue(I, I.P, ps, map2(Dn, (long long)DE * p6, E),
-                                     map3(E, E, 1, p6, (long long)E * p6));
+                                     map3(E, E, 1, p6, (long long)E * p6), I.sPop);
     if (tc_gemm(I.mode, a, b, D * Dn, D * E2, D, ep, I.err, I.s) != cudaSuccess) return 1;
   }
   hook->launched(HOTRG_ST_PROJ_P, 1);
@@ -225,11 +242,11 @@ int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long
   // a6: Q[(a,y,y')][(x1',x2')] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
   hook->begin(HOTRG_ST_PROJ_Q);
   {
-    TcOperand a{I.P, Dn * DE, DE, p6}, b{I.opT6, DE, DE, p6};
+    TcOperand a = operand(I, I.P, Dn * DE, DE, p6, I.sPop), b = operand(I, I.opT6, DE, DE, p6, I.sTop);
     const long long ps = (long long)Dn * E2 * p7;
     TcEpilogue ep = operand_epilogue(I, I.Q, ps,
                                      map3(E, D, (long long)E * p7, D, (long long)E2 * p7),
-                                     map2(D, 1, p7));
+                                     map2(D, 1, p7), I.sPop);
     if (tc_gemm(I.mode, a, b, Dn * DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
   }
   hook->launched(HOTRG_ST_PROJ_Q, 1);
@@ -237,8 +254,8 @@ int TcPath::project(const double *T, const double *U, int D, int E, int Dn, long
   // a7: T'(m = (a,y,y'), b) = sum_{(x1',x2')} Q[m][(x1',x2')] U[(x1' x2'), b]
   hook->begin(HOTRG_ST_PROJ_T);
   {
-    TcOperand a{I.Q, Dn * E2, n, p7}, b{I.opU7, Dn, n, p7};
-    if (tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn), I.err, I.s) !=
+    TcOperand a = operand(I, I.Q, Dn * E2, n, p7, I.sPop), b = operand(I, I.opU7, Dn, n, p7, I.sTop);
+    if (tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn, sTout), I.err, I.s) !=
         cudaSuccess)
       return 1;
   }

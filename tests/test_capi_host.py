@@ -73,3 +73,27 @@ def test_host_argument_validation(lib):
     assert lib.hotrg_step(None, 0) == HOTRG_EINVAL
     lib.hotrg_destroy(None)   # NULL-safe
     assert pkg.status_string(HOTRG_EINVAL) == "HOTRG_EINVAL"
+
+
+def test_batch_argument_validation(lib):
+    from paper_2602_05900_gb300.capi import HOTRG_EINVAL
+    bufs = [np.zeros(16), np.zeros(16)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    ptrs = (dp * 2)(*[b.ctypes.data_as(dp) for b in bufs])
+    d0 = (ctypes.c_int * 2)(2, 2)
+    h = ctypes.c_void_p()
+    # rejected before any device work: count, NULL arrays, sizes, precision
+    assert lib.hotrg_batch_create(0, ptrs, d0, (ctypes.c_int * 2)(8, 8), 1, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_batch_create(4097, ptrs, d0, (ctypes.c_int * 2)(8, 8), 1, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_batch_create(2, None, d0, (ctypes.c_int * 2)(8, 8), 1, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_batch_create(2, ptrs, d0, (ctypes.c_int * 2)(8, 65), 1, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_batch_create(2, ptrs, (ctypes.c_int * 2)(2, 0), (ctypes.c_int * 2)(8, 8), 1, None,
+                                  ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_batch_create(2, ptrs, d0, (ctypes.c_int * 2)(8, 8), 7, None, ctypes.byref(h)) == HOTRG_EINVAL
+    nullptrs = (dp * 2)(bufs[0].ctypes.data_as(dp), dp())
+    assert lib.hotrg_batch_create(2, nullptrs, d0, (ctypes.c_int * 2)(8, 8), 1, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert h.value is None
+    n = ctypes.c_int()
+    assert lib.hotrg_batch_size(None, ctypes.byref(n)) == HOTRG_EINVAL
+    assert lib.hotrg_batch_step(None, 0) == HOTRG_EINVAL
+    assert lib.hotrg_batch_log_z(None, None) == HOTRG_EINVAL

@@ -1,0 +1,106 @@
+"""GPU parity of batched contexts (hotrg_batch_*): many independent instances
+with different couplings, cuts and initial bond dimensions in one context.
+
+Every instance of a batch must give the oracle's ln Z / N to the same
+tolerance as a context of its own, its step bookkeeping must match, and a
+batch instance must agree with the same instance run alone on the GPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import hotrg as ref
+from workloads import BETA_C_POTTS3, sweep256
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = {"tf32": 5e-4, "bf16x3": 5e-5, "bf16x6": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_05900_gb300 as p
+    p.load()
+    return p
+
+
+def instances():
+    """Seeded mix: Ising betas from the sweep's distribution (two of them with a
+    field), cuts spanning the direct-Jacobi and subspace-iteration eigensolver
+    paths, and one q=3 Potts instance (D0 = 3, a group of its own)."""
+    sw = sweep256()
+    out = []
+    for i, d in enumerate([8, 12, 8, 16, 12, 8]):
+        h = 0.01 if i in (1, 4) else 0.0
+        out.append(("ising", sw[i].beta, h, d))
+    out.append(("potts", BETA_C_POTTS3, 0.0, 9))
+    return out
+
+
+def oracle_t0(kind, beta, h):
+    return ref.ising_initial_tensor(beta, h) if kind == "ising" else ref.potts_initial_tensor(3, beta)
+
+
+def gpu_t0(pkg, kind, beta, h):
+    return pkg.ising_tensor(beta, h) if kind == "ising" else pkg.potts_tensor(3, beta)
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    return [ref.run(oracle_t0(k, b, h), d, 12) for k, b, h, d in instances()]
+
+
+def test_fp64_batch_vs_oracle(pkg, oracle_runs):
+    inst = instances()
+    with pkg.HotrgBatch([gpu_t0(pkg, k, b, h) for k, b, h, _ in inst], [d for *_, d in inst], "fp64") as bt:
+        assert bt.size() == len(inst)
+        bt.run(12)
+        lz = bt.ln_z_per_site()
+        for i, r in enumerate(oracle_runs):
+            assert abs(lz[i] / r.ln_z_per_site - 1) < 1e-12, (i, lz[i], r.ln_z_per_site)
+            for s_i, s in enumerate(r.steps):
+                info = bt.step_info(i, s_i)
+                assert (info.Dx, info.Dy, info.Dn) == (s.Dx, s.Dy, s.Dn)
+                # Tr G of a step scales with the previous max-norm, which is
+                # gauge-dependent when kept eigenvalues are degenerate (the S3
+                # multiplets of the Potts model): compared for Ising only
+                if inst[i][0] == "ising":
+                    assert abs(info.trace_G / s.trace_G - 1) < 1e-10, (i, s_i, info.trace_G, s.trace_G)
+            T = bt.tensor(i)
+            assert T.shape == r.T.shape
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_mixed_batch_vs_oracle_and_single(pkg, oracle_runs, prec):
+    inst = instances()
+    with pkg.HotrgBatch([gpu_t0(pkg, k, b, h) for k, b, h, _ in inst], [d for *_, d in inst], prec) as bt:
+        bt.run(12)
+        lz = bt.ln_z_per_site()
+    for i, ((k, b, h, d), r) in enumerate(zip(inst, oracle_runs)):
+        err = abs(lz[i] / r.ln_z_per_site - 1)
+        print(f"instance {i} ({k}, beta={b:.4f}, D_cut={d}) {prec}: relative error {err:.3e}")
+        assert err < MIXED_TOL[prec]
+        with pkg.Hotrg(gpu_t0(pkg, k, b, h), d, prec) as one:
+            one.run(12)
+            single = one.ln_z_per_site()
+        # same kernels and operand rounding; only eigensolver iteration counts may differ
+        assert abs(lz[i] / single - 1) < 1e-9, (i, lz[i], single)
+
+
+def test_batch_of_one_matches_single_context(pkg):
+    T0 = pkg.ising_tensor(0.44, 0.0)
+    with pkg.HotrgBatch([T0], [16], "fp64") as bt, pkg.Hotrg(T0, 16, "fp64") as one:
+        bt.run(10)
+        one.run(10)
+        assert bt.ln_z_per_site()[0] == one.ln_z_per_site()
+        assert np.array_equal(bt.tensor(0), one.tensor())
+
+
+def test_batch_rejects_zero_instance_tensor(pkg):
+    from paper_2602_05900_gb300.capi import HOTRG_ENONFINITE
+    T0 = pkg.ising_tensor(0.44, 0.0)
+    with pytest.raises(pkg.HotrgError) as e:
+        pkg.HotrgBatch([T0, np.zeros_like(T0)], [8, 8], "fp64")
+    assert e.value.status == HOTRG_ENONFINITE
