@@ -11,6 +11,11 @@ the library's stream, each preceded by an L2 flush outside the events.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--precision fp64|tf32|bf16x3|bf16x6] [--impl ours|reference]
 
+``--workload sweep256`` times the batched beta sweep instead: 256 Ising
+instances (seeded beta in [0.35, 0.55], D_cut in {16, 24, 32, 40}) in one
+batched context; a step advances every instance once and the value is
+instance-steps per second.
+
 N > 1 (torchrun) runs N independent replicas, one per GPU (an RG step of
 one instance does not shard); the value is the total over ranks divided by
 the slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle on
@@ -31,9 +36,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import CONFIGS  # noqa: E402
+from workloads import CONFIGS, sweep256  # noqa: E402
 
 METRIC = "HOTRG RG-steps/s at steady-state D=D_cut (TF32 tensor-core contractions, FP64 eig)"
+SWEEP_METRIC = "HOTRG aggregate RG-steps/s, batched beta sweep (instance-steps/s, TF32 contractions, FP64 eig)"
+EIG_NOTE = ("fp64 batched subspace iteration + two-sided Jacobi Rayleigh-Ritz (top D'+1 pairs, "
+            "both sides), cuSOLVER syevdx fallback")
 L2_FLUSH_BYTES = 512 << 20
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor throughput
 BF16_SPLIT_PRODUCTS = {"bf16x3": 3, "bf16x6": 6}
@@ -259,7 +267,7 @@ def run_ours(args, world, rank, local):
            "data": "synthetic (analytic Ising/Potts initial tensor; no dataset)",
            "config": {"workload": cfg.name, "family": cfg.family, "beta": cfg.beta, "h": cfg.h,
                       "q": cfg.q, "D_cut": D, "steady_state_D": D, "precision": prec,
-                      "eig": "fp64 cuSOLVER syevdx (top D'+1 pairs, both sides)",
+                      "eig": EIG_NOTE,
                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write) and "
                             f"per-step working set > L2", "parallelism": f"replicas x{world}"},
            "tflops": round(flops_step * world * args.steps / (max_ms / 1e3) / 1e12, 3),
@@ -338,12 +346,146 @@ def cpu_baseline(cfg, budget_s=20.0, max_steps=8):
                       f"steps (NumPy/OpenBLAS FP64, {dt:.1f} s)"}
 
 
+# ----------------------------------------------------------------------------- batched sweep
+
+def transient_steps(D0, D_cut, first="x"):
+    """Steps until Dx = Dy = D_cut (each step squares the fused dimension, capped)."""
+    dx = dy = D0
+    d, n = first, 0
+    while not (dx == D_cut and dy == D_cut):
+        if d == "x":
+            dy = min(dy * dy, D_cut)
+        else:
+            dx = min(dx * dx, D_cut)
+        d = "y" if d == "x" else "x"
+        n += 1
+    return n
+
+
+def sweep_batch(pkg, models, prec, stream):
+    T0s = [pkg.ising_tensor(m.beta, m.h) for m in models]
+    return pkg.HotrgBatch(T0s, [m.D_cut for m in models], prec, stream)
+
+
+def run_sweep(args, world, rank, local):
+    import torch
+    import paper_2602_05900_gb300 as pkg
+    pkg.load()
+    torch.cuda.set_device(local)
+    models = sweep256()
+    prec = args.precision or models[0].precision
+    n = len(models)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ntr = max(transient_steps(2, m.D_cut) for m in models)
+    bt = sweep_batch(pkg, models, prec, stream)
+    d = "x"
+    for _ in range(ntr):
+        bt.step(d)
+        d = "y" if d == "x" else "x"
+    _, d = time_steps(torch, bt, d, args.warmup, stream, flush)
+    bt.profile_enable(True)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times, d = time_steps(torch, bt, d, args.steps, stream, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof = bt.profile_read()
+    bt.close()
+    max_ms = reduce_max(sum(times), world)
+    value = world * n * args.steps / (max_ms / 1e3)
+    flops_step = sum(step_flops(m.D_cut, m.D_cut, m.D_cut) for m in models)
+    q_flops = sum(2.0 * m.D_cut ** 7 for m in models)          # a6 flops of one batch step
+    q_ms_step = prof["ms"]["proj_q"] / max(1, prof["steps"])
+    achieved = q_flops / (q_ms_step / 1e3) / 1e12
+    bf16_burst, _, _, peak_src = peaks()
+    peak = bf16_burst * TF32_PER_BF16 if prec == "tf32" else bf16_burst / BF16_SPLIT_PRODUCTS.get(prec, 1)
+    cuts = sorted({m.D_cut for m in models})
+    out = {"metric": SWEEP_METRIC, "value": round(value, 3), "unit": "RG-steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": prec, "data": "synthetic (analytic Ising initial tensors, seeded betas; no dataset)",
+           "config": {"workload": "sweep256", "instances": n, "D_cuts": cuts,
+                      "beta_range": [0.35, 0.55], "precision": prec, "groups": len(cuts),
+                      "transient_steps": ntr, "eig": EIG_NOTE,
+                      "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)",
+                      "parallelism": f"replicas x{world}"},
+           "tflops": round(flops_step * world * args.steps / (max_ms / 1e3) / 1e12, 3),
+           "roofline": {"kernel": "k_tc_gemm a6 bond contraction Q=P.T (all groups of a step)",
+                        "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                        "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                        "peak_source": f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"},
+           "stage_ms_per_step": {k: round(v / max(1, prof["steps"]), 4) for k, v in prof["ms"].items()},
+           "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
+    if rank == 0 and not args.quick:
+        out["e2e"] = sweep_e2e(pkg, models, prec, torch)
+        out["cpu_baseline"] = sweep_cpu_baseline(models, budget_s=args.cpu_budget)
+    return out
+
+
+def sweep_e2e(pkg, models, prec, torch):
+    """The whole sweep job from host memory: host T0s -> batch create (H2D) ->
+    25 steps -> ln Z / N of every instance (D2H)."""
+    steps = models[0].steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with sweep_batch(pkg, models, prec, None) as bt:
+        bt.run(steps)
+        lz = bt.ln_z_per_site()
+    dt = time.perf_counter() - t0
+    n = len(models)
+    return {"value": round(n * steps / dt, 3), "unit": "RG-steps/s",
+            "h2d_bytes_per_step": round(n * 16 * 8 / steps, 2),
+            "d2h_bytes_per_step": round((n * 8 * 8 + 4 * steps) / steps, 2),
+            "ln_z_finite": bool(all(math.isfinite(v) for v in lz)),
+            "note": f"full {steps}-step job of {n} instances incl. creation and transient steps"}
+
+
+def sweep_cpu_baseline(models, budget_s=20.0):
+    """The FP64 oracle on the host cores: one steady-state step per distinct
+    D_cut, weighted by how many instances have that cut."""
+    from oracle import hotrg as ref
+    per_cut = {}
+    t_all = time.perf_counter()
+    for m in models:
+        if m.D_cut in per_cut:
+            continue
+        T = ref.ising_initial_tensor(m.beta, m.h)
+        T = T / abs(T).max()
+        d = "x"
+        for _ in range(transient_steps(2, m.D_cut)):
+            T = (ref.x_step if d == "x" else ref.y_step)(T, m.D_cut)[0]
+            d = "y" if d == "x" else "x"
+        t0 = time.perf_counter()
+        (ref.x_step if d == "x" else ref.y_step)(T, m.D_cut)
+        per_cut[m.D_cut] = time.perf_counter() - t0
+    sec_per_batch_step = sum(per_cut[m.D_cut] for m in models)
+    return {"value": round(len(models) / sec_per_batch_step, 4), "unit": "RG-steps/s",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one steady-state oracle step per D_cut in " + str(sorted(per_cut)) +
+                      f", weighted by instance count ({time.perf_counter() - t_all:.1f} s incl. transients)"}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank):
-    cfg = CONFIGS[args.workload]
     if rank != 0:
         return None
+    if args.workload == "sweep256":
+        models = sweep256()
+        sweep_cpu_baseline(models[:1])                      # warm-up (untimed)
+        vals = [sweep_cpu_baseline(models) for _ in range(max(1, min(args.steps, 2)))]
+        v = statistics.median([x["value"] for x in vals])
+        return {"metric": SWEEP_METRIC, "value": v, "unit": "RG-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(len(models) * 1e3 / v, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "impl": "reference", "data": "synthetic (analytic Ising initial tensors, seeded betas; no dataset)",
+                "config": {"workload": "sweep256", "precision": "fp64 (CPU oracle)"},
+                "cpu_baseline": vals[-1],
+                "e2e": {"value": v, "unit": "RG-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    cfg = CONFIGS[args.workload]
     budget = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     # each step: one steady-state oracle step (a bounded sample of the workload)
     base = cpu_baseline(cfg, budget_s=0.0, max_steps=args.warmup)   # warm-up steps (untimed value)
@@ -367,7 +509,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="ising_044_d32", choices=sorted(CONFIGS))
+    ap.add_argument("--workload", default="ising_044_d32", choices=sorted(CONFIGS) + ["sweep256"])
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU legs")
@@ -387,6 +529,8 @@ def main():
             dist.init_process_group("nccl")
     if args.impl == "reference":
         out = run_reference(args, world, rank)
+    elif args.workload == "sweep256":
+        out = run_sweep(args, world, rank, local)
     else:
         out = run_ours(args, world, rank, local)
     if rank == 0 and out is not None:

@@ -63,3 +63,13 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "RG-steps/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_transient_steps_schedule():
+    import bench
+    # each step squares the fused dimension (capped at D_cut): 2 -> 4 -> 16 -> D_cut
+    assert bench.transient_steps(2, 16) == 4
+    assert bench.transient_steps(2, 24) == 6
+    assert bench.transient_steps(2, 40) == 6
+    assert bench.transient_steps(2, 4) == 2
+    assert bench.transient_steps(3, 9) == 2
