@@ -164,6 +164,17 @@ hotrg_status hotrg_get_isometry(hotrg_ctx *ctx, double *host_out, long long cap,
 hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
 
 /*
+ * Context options (set between steps; they take effect at the next step).
+ *   HOTRG_OPT_EIG_TC_PRODUCTS  1 (default): the eigensolver's products G X run
+ *       on the BF16 tensor cores as exact-slice FP64-grade GEMMs (eight base-64
+ *       digits per operand row, see hotrg_dgemm_emu); 0: FP64 SIMT kernels.
+ *       Either way the eigenpairs meet the same residual bound.
+ * Returns HOTRG_EINVAL for an unknown option or value.
+ */
+enum { HOTRG_OPT_EIG_TC_PRODUCTS = 0 };
+hotrg_status hotrg_set_option(hotrg_ctx *ctx, int option, int value);
+
+/*
  * Stage profiler (tracing, no effect on results).  Stages of one step
  * (Sec. II.A splits the cost into contraction and SVD; the contraction is
  * split further here):
@@ -256,6 +267,29 @@ hotrg_status hotrg_batch_log_z(hotrg_ctx *ctx, double *out_n);
 hotrg_status hotrg_batch_step_info(hotrg_ctx *ctx, int inst, int step, hotrg_step_info_t *out);
 hotrg_status hotrg_batch_get_tensor(hotrg_ctx *ctx, int inst, double *host_out, long long cap,
                                     int dims[4]);
+
+/*
+ * FP64-grade GEMM on the BF16 tensor cores (the paper has no counterpart; the
+ * library's eigensolver uses the same kernels for its products G X, because
+ * GB300 runs native FP64 at about 1 TFLOP/s):
+ *   C[i * ldc + j] = sum_k A[i * lda + k] * B[j * ldb + k],  0 <= i < M, 0 <= j < N
+ * (row-major A: M x K, B: N x K, C: M x N, all FP64 device pointers that stay
+ * owned by the caller; C must not overlap A or B).  Each row of A and of B is
+ * scaled by a power of two below 1 and cut into `slices` base-64 digits
+ * stored as exact BF16 values; products of digit pairs whose indices sum to at
+ * most slices + 1 are accumulated on the tensor cores, exactly for the five
+ * leading digit sums (K is split into parts of at most 2336 for that), and
+ * combined in 64-bit integer and FP64 arithmetic.  Error per term about
+ * 2^-(6 slices) relative to the row maxima max|A_i.| max|B_j.| (slices = 8:
+ * about 1e-15 of max|A_i.| max|B_j.| K).  4 <= slices <= 8, K >= 1, lda, ldb >= K, ldc >= N.  Allocates its scratch
+ * (about 2 slices (M + N) K bytes) with cudaMalloc, runs on `stream` and
+ * synchronises it before returning.  Returns HOTRG_OK, HOTRG_EINVAL,
+ * HOTRG_ENOMEM, HOTRG_ECUDA, or HOTRG_ETIMEOUT if a bounded device wait ran
+ * out.  A row with a non-finite entry gives NaN in its outputs.
+ */
+hotrg_status hotrg_dgemm_emu(int M, int N, int K, const double *A, long long lda,
+                             const double *B, long long ldb, double *C, long long ldc,
+                             int slices, void *stream);
 
 /* Release all resources of the context; NULL is accepted and ignored. */
 void hotrg_destroy(hotrg_ctx *ctx);

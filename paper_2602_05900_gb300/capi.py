@@ -23,6 +23,9 @@ DIR_X, DIR_Y = 0, 1
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3}
 
 
+OPT_EIG_TC_PRODUCTS = 0
+
+
 class StepInfo(ctypes.Structure):
     """Mirror of ``hotrg_step_info_t``."""
     _fields_ = [("dir", ctypes.c_int), ("Dx", ctypes.c_int), ("Dy", ctypes.c_int),
@@ -78,6 +81,10 @@ _SIGS = {
                                              ctypes.POINTER(StepInfo)]),
     "hotrg_batch_get_tensor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_longlong,
                                               _ip]),
+    "hotrg_dgemm_emu": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong,
+                                       ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p]),
+    "hotrg_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hotrg_destroy": (None, [ctypes.c_void_p]),
     "hotrg_rescale_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_void_p]),
@@ -209,6 +216,9 @@ class Hotrg:
                                               ctypes.byref(cols)), "hotrg_get_isometry")
         return out.reshape(cols.value, rows.value).T.copy()   # column-major -> [row, col]
 
+    def set_option(self, option: int, value: int):
+        self._check(load().hotrg_set_option(self._h, option, value), "hotrg_set_option")
+
     def profile_enable(self, on: bool = True):
         self._check(load().hotrg_profile_enable(self._h, 1 if on else 0), "hotrg_profile_enable")
 
@@ -273,6 +283,7 @@ class HotrgBatch:
     __enter__ = Hotrg.__enter__
     __exit__ = Hotrg.__exit__
     profile_enable = Hotrg.profile_enable
+    set_option = Hotrg.set_option
     profile_read = Hotrg.profile_read
 
     def step(self, direction: str):
@@ -304,3 +315,18 @@ class HotrgBatch:
         self._check(load().hotrg_batch_get_tensor(self._h, inst, _ptr(out), out.size, dims),
                     "hotrg_batch_get_tensor")
         return out
+
+
+def dgemm_emu(A, B, C, slices: int = 7, stream=None):
+    """C = A @ B.T through ``hotrg_dgemm_emu`` on torch CUDA float64 tensors
+    (row-major, unit column stride); returns C."""
+    for t in (A, B, C):
+        if t.dtype.itemsize != 8 or not t.is_cuda or t.stride(1) != 1:
+            raise ValueError("A, B, C must be float64 CUDA tensors with unit column stride")
+    M, K = A.shape
+    N = B.shape[0]
+    s = load().hotrg_dgemm_emu(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                               C.data_ptr(), C.stride(0), slices, _stream_handle(stream))
+    if s:
+        raise HotrgError(s, f"hotrg_dgemm_emu failed: {status_string(s)}")
+    return C

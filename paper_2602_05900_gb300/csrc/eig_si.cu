@@ -5,6 +5,16 @@
 // two environments of a step run in the same launches), and only the small
 // m x m factorisations run on one CTA per problem.
 //
+// The iteration runs on G + sigma I with sigma = 2^-40 Tr G (same
+// eigenvectors; the Ritz values are shifted back at the end).  The shift keeps
+// the columns of G X that belong to the numerical null space of G at least
+// sigma long and along their own direction when the products are nearly
+// exact (HOTRG fixed points far from criticality have numerically rank
+// deficient G).  Where columns still become nearly dependent (G from
+// reduced-precision contractions is indefinite at their rounding level, and a
+// Ritz value can sit at zero), the FP32 CholeskyQR pass restarts with a shift
+// instead of breaking down.
+//
 // One iteration:  Y = G X  ->  X = orth(Y): shifted CholeskyQR3 in FP64 until
 // the first Rayleigh-Ritz step, two FP32 CholeskyQR passes (FP64 rotation)
 // after it.  Before each Rayleigh-Ritz step two FP64 Newton-Schulz steps make
@@ -20,6 +30,7 @@
 #include <cooperative_groups.h>
 
 #include "eig_si.cuh"
+#include "tc_exact.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -32,6 +43,7 @@ constexpr int kRowsPerChunk = 16;
 constexpr int kCluster = 8;      // CTAs per Jacobi problem (one thread-block cluster)
 constexpr int kJacobiMaxSweeps = 40;
 constexpr int kCholThreads = 256;
+constexpr float kChol32Retry = 0x1.0p-12f;   // diagonal shift of a retried FP32 CholeskyQR pass
 
 
 // splitmix64 finaliser (Steele, Lea, Flood 2014) -> uniform double in [-1, 1)
@@ -130,6 +142,36 @@ __global__ void __launch_bounds__(256) k_si_gemm(PSet G, PSet X, PSet Out, int n
       if (j < m) out[(size_t)j * n + i] = acc[c];
     }
   }
+}
+
+// Shift of the iteration (see si_solve): sig[0] is the shift of the current
+// Y = (G + sig[0] I) X, sig[1] the shift of the next product (equal to it in
+// this solver; kept apart so that a shift change can never mix the two).
+__global__ void k_si_sigma_init(PSet sig, PSet trace, double factor) {
+  const int z = blockIdx.z;
+  if (threadIdx.x == 0) {
+    const double t = trace.at(z)[0];
+    const double v = (t > 0.0 && isfinite(t)) ? factor * t : 0.0;
+    sig.at(z)[0] = v;
+    sig.at(z)[1] = v;
+  }
+}
+
+// Y += sig[1] X; block (0, 0, z) records sig[0] = sig[1] (the shift now in Y)
+__global__ void k_si_shift_add(PSet Y, PSet X, PSet sig, long long nm) {
+  const int z = blockIdx.z;
+  const double sg = sig.at(z)[1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
+       e += (long long)gridDim.x * blockDim.x)
+    Y.at(z)[e] = fma(sg, X.at(z)[e], Y.at(z)[e]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sig.at(z)[0] = sg;
+}
+
+// theta_z[i] -= sig[0] for i < m (the shift of the last Rayleigh-Ritz step)
+__global__ void k_si_unshift(PSet theta, PSet sig, int m) {
+  const int z = blockIdx.z;
+  const double sg = sig.at(z)[0];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) theta.at(z)[i] -= sg;
 }
 
 __global__ void k_si_sum_split(PSet part, PSet out, int S, long long nm) {
@@ -258,32 +300,40 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
     const double cjj = Cin.at(z)[(size_t)j * m + j];
     d[j] = (cjj > 0.0 && isfinite(cjj)) ? (float)rsqrt_fp64(cjj) : 1.0f;
   }
-  __syncthreads();
-  for (int a = ty; a < m; a += 16)
-    for (int b = tx; b < m; b += 16)
-      C[a * ld + b] = (float)Cin.at(z)[(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? shift : 0.0f);
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    const float piv = C[j * ld + j];
-    if (!(piv > 0.0f) || !isfinite(piv)) {
-      if (threadIdx.x == 0) bad = 1;
-      break;
+  // A nearly dependent set of columns breaks the unshifted factorisation; the
+  // second attempt adds kChol32Retry to the unit diagonal, which always
+  // succeeds and leaves a basis with condition number below about
+  // kChol32Retry^-1/2 for the next pass to finish.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const float sh = attempt == 0 ? shift : fmaxf(shift, kChol32Retry);
+    __syncthreads();
+    for (int a = ty; a < m; a += 16)
+      for (int b = tx; b < m; b += 16)
+        C[a * ld + b] = (float)Cin.at(z)[(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? sh : 0.0f);
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      const float piv = C[j * ld + j];
+      if (!(piv > 0.0f) || !isfinite(piv)) {
+        if (threadIdx.x == 0) bad = 1;
+        break;
+      }
+      const float ri = rsqrtf(piv);
+      __syncthreads();
+      for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) C[j * ld + l] *= ri;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        C[j * ld + j] = piv * ri;
+        rinv[j] = ri;
+      }
+      for (int a = j + 1 + ty; a < m; a += 16)
+        for (int b = a + tx; b < m; b += 16) C[a * ld + b] = fmaf(-C[j * ld + a], C[j * ld + b], C[a * ld + b]);
+      __syncthreads();
     }
-    const float ri = rsqrtf(piv);
     __syncthreads();
-    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) C[j * ld + l] *= ri;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      C[j * ld + j] = piv * ri;
-      rinv[j] = ri;
-    }
-    for (int a = j + 1 + ty; a < m; a += 16)
-      for (int b = a + tx; b < m; b += 16) C[a * ld + b] = fmaf(-C[j * ld + a], C[j * ld + b], C[a * ld + b]);
-    __syncthreads();
+    if (!bad) break;
   }
-  __syncthreads();
   if (bad) {
     if (threadIdx.x == 0) atomicExch(flag, 1);
     return;
@@ -636,9 +686,18 @@ __global__ void __launch_bounds__(256) k_si_rotate(PSet A, PSet W, PSet Out, int
 }
 
 // res[i] = ||Y_i - theta_i X_i|| / |theta_0|, i < k
-__global__ void k_si_residual(PSet X, PSet Y, PSet theta, PSet res, int n, int k) {
+// res_i = ||y_i - theta_i x_i|| / theta_0, or 0 for a pair whose unshifted
+// value lies below half the shift (2^-41 Tr G: inside the band where G's own
+// rounding makes the eigenpairs arbitrary; any orthonormal completion there
+// is as good as another)
+__global__ void k_si_residual(PSet X, PSet Y, PSet theta, PSet res, PSet sig, int use_sig, int n,
+                              int k) {
   const int z = blockIdx.z, i = blockIdx.x;
   const double th = theta.at(z)[i];
+  if (use_sig && th - sig.at(z)[0] <= 0.5 * sig.at(z)[1] && i > 0) {
+    if (threadIdx.x == 0) res.at(z)[i] = 0.0;
+    return;
+  }
   const double *x = X.at(z) + (size_t)i * n;
   const double *y = Y.at(z) + (size_t)i * n;
   double v = 0.0;
@@ -690,7 +749,10 @@ struct Layout {
   long long nm, mm;
   long long per;   // doubles per problem
   // slot offsets (doubles) inside a problem's workspace
-  long long oY, oZ, oX, oYp, oCp, oC, oW, oRes, oTh;
+  long long oY, oZ, oX, oYp, oCp, oC, oW, oRes, oTh, oSig;
+  // exact-slice operands of G X (BF16 slices of G and X^T, row scales)
+  int xsp;
+  long long oGs, oGsc, oXs, oXsc;
 };
 
 Layout layout(int P, int n, int m) {
@@ -713,12 +775,18 @@ Layout layout(int P, int n, int m) {
   L.oW = o; o += up(L.mm);
   L.oRes = o; o += up(m);
   L.oTh = o; o += up(m);
+  L.oSig = o; o += up(2);
+  L.xsp = xs_pitch(n);
+  L.oGs = o; o += up((xs_elems(n, n, kSiSlices) + 3) / 4);
+  L.oGsc = o; o += up(n);
+  L.oXs = o; o += up((xs_elems(m, n, kSiSlices) + 3) / 4);
+  L.oXsc = o; o += up(m);
   L.per = o;
   return L;
 }
 
 struct Bufs {
-  PSet Y, Z, X, Yp, Cp, C, W, res, th;
+  PSet Y, Z, X, Yp, Cp, C, W, res, th, sig;
   int *flag, *sweeps;
 };
 
@@ -733,6 +801,7 @@ Bufs carve(double *work, int P, const Layout &L) {
   B.W = pset_linear(work + L.oW, L.per);
   B.res = pset_linear(work + L.oRes, L.per);
   B.th = pset_linear(work + L.oTh, L.per);
+  B.sig = pset_linear(work + L.oSig, L.per);
   B.flag = reinterpret_cast<int *>(work + (long long)P * L.per);
   B.sweeps = B.flag + 2;
   return B;
@@ -834,7 +903,41 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16;
   long long nl = 0;
 
-  auto gemm = [&](PSet src, PSet dst) {
+  // Y = G X.  Exact-slice tensor-core products (FP64-grade, see tc_exact.cuh)
+  // unless the caller asked for the FP64 SIMT kernel.
+  const bool xs = b.xs;
+  XsOperand gs{}, xsl{};
+  int xsplit = 1;
+  if (xs) {
+    gs = XsOperand{work + L.oGs, work + L.oGsc, n, n, L.xsp, kSiSlices, P, L.per * 4, L.per};
+    xsl = XsOperand{work + L.oXs, work + L.oXsc, m, n, L.xsp, kSiSlices, P, L.per * 4, L.per};
+    const int tiles = ((n + 127) / 128) * ((m + 95) / 96) * P;
+    xsplit = std::max(xs_min_split(n), std::min(kSplitMax, (2 * 152 + tiles - 1) / tiles));
+    while (xsplit > xs_min_split(n) && (n + xsplit - 1) / xsplit < 256) --xsplit;
+    if ((e = xs_split(b.G, map1(n), map1(1), gs, s))) return e;
+    nl += 1;
+  }
+  auto add_shift = [&](PSet src, PSet dst) -> cudaError_t {
+    if (!b.has_trace) return cudaSuccess;
+    k_si_shift_add<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(dst, src, B.sig, L.nm);
+    nl += 1;
+    return cudaGetLastError();
+  };
+  auto product = [&](PSet src, PSet dst) -> cudaError_t {
+    if (xs) {
+      cudaError_t r = xs_split(src, map1(n), map1(1), xsl, s);
+      if (r) return r;
+      if (xsplit == 1) {
+        r = xs_gemm(gs, xsl, n, m, n, dst.b0, map1(1), map1(n), L.per, 1, 0, b.err, s);
+        nl += 2;
+      } else {
+        r = xs_gemm(gs, xsl, n, m, n, B.Yp.b0, map1(1), map1(n), L.per, xsplit, L.nm, b.err, s);
+        if (r) return r;
+        k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, xsplit, L.nm);
+        nl += 3;
+      }
+      return r ? r : cudaGetLastError();
+    }
     if (L.S == 1) {
       k_si_gemm<<<dim3((n + 63) / 64, 1, P), 256, 0, s>>>(b.G, src, dst, n, m, chunk);
       nl += 1;
@@ -843,6 +946,11 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, L.S, L.nm);
       nl += 2;
     }
+    return cudaGetLastError();
+  };
+  auto gemm = [&](PSet src, PSet dst) -> cudaError_t {
+    cudaError_t r0 = product(src, dst);
+    return r0 ? r0 : add_shift(src, dst);
   };
   // C = A^T B (m x m), symmetrised; ns: write the Newton-Schulz polish (3I - C)/2 instead
   auto gram = [&](PSet A, PSet Bm, bool sym, bool f32, bool ns) {
@@ -890,6 +998,10 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   };
 
   if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
+  if (b.has_trace) {
+    k_si_sigma_init<<<dim3(1, 1, P), 32, 0, s>>>(B.sig, b.trace, b.shift_rel);
+    nl += 1;
+  }
   k_si_init<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(X, b.warm, b.has_warm ? 1 : 0, b.kw, n, m);
   nl += 1;
   cholqr32(X, Z, 0.0f);             // a random start is well conditioned
@@ -908,7 +1020,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       polish(X, Z);
       polish(Z, X);
     }
-    gemm(X, Y);                     // Y = G X
+    if ((e = gemm(X, Y))) return e;  // Y = G X
     ++it;
     if (check) {
       gram(X, Y, false, false, false);   // H = X^T G X
@@ -917,7 +1029,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       std::swap(X, Z);
       k_si_rotate<<<grot, 256, 0, s>>>(Y, B.W, Z, n, m, 0);
       std::swap(Y, Z);
-      k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, n, k);
+      k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, B.sig, b.has_trace ? 1 : 0, n, k);
       nl += 4;
       ++res->rr;
       if ((e = cudaMemcpy2DAsync(hres.data(), sizeof(double) * k, B.res.at(0), sizeof(double) * L.per,
@@ -952,6 +1064,10 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     orth(Y, Z, X, res->rr > 0);     // X = orth(G X)
   }
   res->iterations = it;
+  if (b.has_trace) {
+    k_si_unshift<<<dim3(1, 1, P), 128, 0, s>>>(B.th, B.sig, m);
+    nl += 1;
+  }
   // the Ritz vectors end in the workspace's X slot
   if (!same(X, B.X)) {
     k_si_copy<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(X, B.X, L.nm);

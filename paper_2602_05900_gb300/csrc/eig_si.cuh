@@ -17,6 +17,7 @@
 namespace hotrg {
 
 constexpr int kSiMaxBlock = 96;    // largest Rayleigh-Ritz block / direct-Jacobi size
+constexpr int kSiSlices = 8;       // exact-slice digits of the products G X
 
 struct SiBatch {
   int P;                 // number of problems
@@ -27,6 +28,11 @@ struct SiBatch {
   PSet warm;             // optional n x kw column-major start vectors of problem z
   bool has_warm;
   int kw;
+  bool xs;               // G X on the tensor cores (exact slices) instead of FP64 SIMT
+  int *err;              // device flag set to 2 if a tensor-core wait runs out (xs only)
+  PSet trace;            // Tr G of problem z at trace.at(z)[0] (iteration shift)
+  bool has_trace;
+  double shift_rel;      // initial shift / Tr G (about the relative accuracy of G)
 };
 
 // Where a solve leaves its results inside the workspace: Ritz vectors of

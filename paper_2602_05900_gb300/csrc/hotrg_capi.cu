@@ -176,6 +176,7 @@ struct hotrg_ctx {
   std::vector<std::unique_ptr<Group>> groups;
   std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
   double *si_work = nullptr;                // eigensolver workspace, shared by the groups
+  bool eig_tc = true;                       // exact-slice tensor-core products G X
   int *err = nullptr;
   hotrg_status status = HOTRG_OK;
   std::string msg;
@@ -454,6 +455,11 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       if (m > kSiMaxBlock) m = kSiMaxBlock;
       if (m > n) m = n & ~1;
       sb.m = m;
+      sb.xs = c->eig_tc;
+      sb.err = c->err;
+      sb.trace = PSet{g.scal + 2, g.scal + 3, kScal};
+      sb.has_trace = true;
+      sb.shift_rel = 0x1.0p-40;
       const int di = ydir ? 1 : 0;
       if (g.nprev[di] == n && g.kprev[di] <= m) {
         // the last isometry of this direction starts both sides' iteration
@@ -686,6 +692,18 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
 }
 
 hotrg_status hotrg_batch_step(hotrg_ctx *c, hotrg_dir dir) { return hotrg_step(c, dir); }
+
+hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->status != HOTRG_OK) return c->status;
+  switch (option) {
+    case HOTRG_OPT_EIG_TC_PRODUCTS:
+      if (value != 0 && value != 1) return HOTRG_EINVAL;
+      c->eig_tc = value != 0;
+      return HOTRG_OK;
+  }
+  return HOTRG_EINVAL;
+}
 
 hotrg_status hotrg_batch_size(hotrg_ctx *c, int *n) {
   if (!c || !n) return HOTRG_EINVAL;

@@ -18,78 +18,12 @@
 #include <mutex>
 
 #include "tc_gemm.cuh"
+#include "tcgen05.cuh"
 
 namespace hotrg {
 namespace {
 
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at the GB300 boost clock
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int c0, int c1, int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile stored with the
-// 128-byte swizzle: rows of 128 bytes, 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
-  d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused with swizzle)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset between 8-row groups
-  d |= static_cast<uint64_t>(1) << 46;            // descriptor version of the sm_100 family
-  d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A/B both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t make_idesc(bool tf32, int M, int N) {
-  return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
-         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
-}
+using namespace tc;
 
 template <bool TF32>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -107,26 +41,6 @@ __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t 
         "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
   }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ float round_tf32(float v) {
@@ -243,9 +157,9 @@ __global__ void __launch_bounds__(128, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = tmem_base_sh;
 
   if (warp == 0 && lane == 0) {
@@ -276,15 +190,15 @@ __global__ void __launch_bounds__(128, 1)
         atomicExch(&s_fail, 1);
         break;
       }
-      tc_fence_after();
+      fence_after();
 #pragma unroll
       for (int k = 0; k < Tr::kBK / Tr::kMmaK; ++k) {
 #pragma unroll
         for (int q = 0; q < Tr::kProducts; ++q) {
           int pa, pb;
           Tr::product(q, pa, pb);
-          const uint64_t ad = sw128_desc(a_tile(s, pa) + k * 32);
-          const uint64_t bd = sw128_desc(b_tile(s, pb) + k * 32);
+          const uint64_t ad = sw_desc<128>(a_tile(s, pa) + k * 32);
+          const uint64_t bd = sw_desc<128>(b_tile(s, pb) + k * 32);
           mma_issue<Tr::kTf32>(tmem, ad, bd, IDESC, (kb | k | q) != 0);
         }
       }
@@ -297,7 +211,7 @@ __global__ void __launch_bounds__(128, 1)
 
   // ---- epilogue: thread (warp w, lane l) owns accumulator row 32 w + l
   const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0);
-  tc_fence_after();
+  fence_after();
   if (!acc_ok) atomicExch(&s_fail, 1);
   const bool ok = acc_ok && (*(volatile int *)&s_fail == 0);
   if (ok) {
@@ -336,7 +250,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   }
 
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_fail) atomicExch(err_flag, 2);
@@ -346,27 +260,13 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncthreads();
   if (warp == 1) {
-    tc_fence_after();
+    fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
                  : "memory");
   }
 }
 
 // ---- host side ----------------------------------------------------------
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
 
 bool make_map(CUtensorMap *m, TcMode mode, const TcOperand &op, int box_rows) {
   auto enc = encode_fn();
@@ -420,6 +320,24 @@ cudaError_t dispatch_bn(const TcOperand &A, const TcOperand &B, int M, int N, in
 }
 
 }  // namespace
+
+namespace tc {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+}  // namespace tc
 
 cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, int N, int K,
                     const TcEpilogue &epi, int *err_flag, cudaStream_t s) {

@@ -14,6 +14,7 @@ from workloads import BETA_C_POTTS3, sweep256
 pytestmark = pytest.mark.gpu
 
 MIXED_TOL = {"tf32": 5e-4, "bf16x3": 5e-5, "bf16x6": 2e-6}
+GAP_TOL = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +60,12 @@ def test_fp64_batch_vs_oracle(pkg, oracle_runs):
         bt.run(12)
         lz = bt.ln_z_per_site()
         for i, r in enumerate(oracle_runs):
-            assert abs(lz[i] / r.ln_z_per_site - 1) < 1e-12, (i, lz[i], r.ln_z_per_site)
+            # a cut inside a degenerate multiplet (relative gap below GAP_TOL) makes
+            # the truncated tensor, and f at the truncation-error level, depend on
+            # the rotation the eigensolver returns: such runs get a looser bound
+            degenerate = min(s.cut_gap for s in r.steps) < GAP_TOL
+            tol = 1e-9 if degenerate else 1e-12
+            assert abs(lz[i] / r.ln_z_per_site - 1) < tol, (i, lz[i], r.ln_z_per_site)
             for s_i, s in enumerate(r.steps):
                 info = bt.step_info(i, s_i)
                 assert (info.Dx, info.Dy, info.Dn) == (s.Dx, s.Dy, s.Dn)

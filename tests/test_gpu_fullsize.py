@@ -57,7 +57,7 @@ def test_fp64_full_job_vs_stored_oracle(pkg, name):
 
 
 @pytest.mark.parametrize("name,prec,tol", [("ising_044_d32", "tf32", 5e-4), ("ising_044h_d48", "bf16x3", 2e-5),
-                                           ("ising_044h_d48", "bf16x6", 2e-6)])
+                                           ("ising_044h_d48", "bf16x6", 2e-6), ("potts3_d64", "bf16x3", 2e-5)])
 def test_mixed_full_job_error_vs_stored_oracle(pkg, name, prec, tol):
     cfg, g = CONFIGS[name], golden(name)
     with pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, prec) as h:
