@@ -43,6 +43,7 @@ constexpr int kRowsPerChunk = 16;
 constexpr int kCluster = 8;      // CTAs per Jacobi problem (one thread-block cluster)
 constexpr int kJacobiMaxSweeps = 40;
 constexpr int kCholThreads = 256;
+constexpr double kXsSmallWork = 32.0 * 1024 * 1024;   // FP64 FMAs of one n x m x m product batch
 constexpr float kChol32Retry = 0x1.0p-12f;   // diagonal shift of a retried FP32 CholeskyQR pass
 
 
@@ -750,9 +751,10 @@ struct Layout {
   long long per;   // doubles per problem
   // slot offsets (doubles) inside a problem's workspace
   long long oY, oZ, oX, oYp, oCp, oC, oW, oRes, oTh, oSig;
-  // exact-slice operands of G X (BF16 slices of G and X^T, row scales)
+  // exact-slice operands (BF16 slices and row scales): G, and two general
+  // slots for the n x m / m x n / m x m operands of the other products
   int xsp;
-  long long oGs, oGsc, oXs, oXsc;
+  long long oGs, oGsc, oSa, oSasc, oSb, oSbsc;
 };
 
 Layout layout(int P, int n, int m) {
@@ -777,10 +779,14 @@ Layout layout(int P, int n, int m) {
   L.oTh = o; o += up(m);
   L.oSig = o; o += up(2);
   L.xsp = xs_pitch(n);
+  const long long sa = std::max(xs_elems(n, m, kSiSlices), xs_elems(m, n, kSiSlices));
+  const long long sb = std::max(xs_elems(m, n, kSiSlices), xs_elems(m, m, kSiSlices));
   L.oGs = o; o += up((xs_elems(n, n, kSiSlices) + 3) / 4);
   L.oGsc = o; o += up(n);
-  L.oXs = o; o += up((xs_elems(m, n, kSiSlices) + 3) / 4);
-  L.oXsc = o; o += up(m);
+  L.oSa = o; o += up((sa + 3) / 4);
+  L.oSasc = o; o += up(std::max(n, m));
+  L.oSb = o; o += up((sb + 3) / 4);
+  L.oSbsc = o; o += up(std::max(n, m));
   L.per = o;
   return L;
 }
@@ -903,17 +909,27 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16;
   long long nl = 0;
 
-  // Y = G X.  Exact-slice tensor-core products (FP64-grade, see tc_exact.cuh)
-  // unless the caller asked for the FP64 SIMT kernel.
+  // Products over the long dimension n (G X, the basis rotations X W and the
+  // Gram matrices X^T Y) run as exact-slice tensor-core GEMMs (FP64-grade, see
+  // tc_exact.cuh) unless the caller asked for the FP64 SIMT kernels.  The
+  // n x m x m rotations and Gram matrices go to the tensor cores only when the
+  // batch makes them FP64-throughput bound (P n m^2 >= kXsSmallWork); below
+  // that the single SIMT launch beats the slice-and-multiply sequence.
   const bool xs = b.xs;
-  XsOperand gs{}, xsl{};
-  int xsplit = 1;
+  const bool xs_small = xs && (double)P * n * m * m >= kXsSmallWork;
+  XsOperand gs{};
+  int xsplit = 1, gsplit = 1;
+  // slices of a row-major (rows x K) view of problem z's buffer at src
+  auto xs_slot = [&](long long off, long long scoff, int rows, int K) {
+    return XsOperand{work + off, work + scoff, rows, K, xs_pitch(K), kSiSlices, P, L.per * 4, L.per};
+  };
   if (xs) {
     gs = XsOperand{work + L.oGs, work + L.oGsc, n, n, L.xsp, kSiSlices, P, L.per * 4, L.per};
-    xsl = XsOperand{work + L.oXs, work + L.oXsc, m, n, L.xsp, kSiSlices, P, L.per * 4, L.per};
     const int tiles = ((n + 127) / 128) * ((m + 95) / 96) * P;
     xsplit = std::max(xs_min_split(n), std::min(kSplitMax, (2 * 152 + tiles - 1) / tiles));
     while (xsplit > xs_min_split(n) && (n + xsplit - 1) / xsplit < 256) --xsplit;
+    const int gtiles = ((m + 79) / 80) * P;
+    gsplit = std::max(xs_min_split(n), std::min(std::min(kChunkMax, n / 64), (2 * 152 + gtiles - 1) / gtiles));
     if ((e = xs_split(b.G, map1(n), map1(1), gs, s))) return e;
     nl += 1;
   }
@@ -925,6 +941,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   };
   auto product = [&](PSet src, PSet dst) -> cudaError_t {
     if (xs) {
+      const XsOperand xsl = xs_slot(L.oSb, L.oSbsc, m, n);     // rows of X^T
       cudaError_t r = xs_split(src, map1(n), map1(1), xsl, s);
       if (r) return r;
       if (xsplit == 1) {
@@ -952,49 +969,80 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     cudaError_t r0 = product(src, dst);
     return r0 ? r0 : add_shift(src, dst);
   };
+  // dst = src W (n x m times m x m, W column-major; tri: W upper triangular)
+  auto rot = [&](PSet src, PSet W, PSet dst, int tri) -> cudaError_t {
+    if (xs_small) {
+      const XsOperand a = xs_slot(L.oSa, L.oSasc, n, m);       // rows of X
+      const XsOperand w = xs_slot(L.oSb, L.oSbsc, m, m);       // columns of W
+      cudaError_t r;
+      if ((r = xs_split(src, map1(1), map1(n), a, s)) || (r = xs_split(W, map1(m), map1(1), w, s)) ||
+          (r = xs_gemm(a, w, n, m, m, dst.b0, map1(1), map1(n), L.per, 1, 0, b.err, s)))
+        return r;
+      nl += 3;
+      return cudaSuccess;
+    }
+    k_si_rotate<<<grot, 256, 0, s>>>(src, W, dst, n, m, tri);
+    nl += 1;
+    return cudaGetLastError();
+  };
   // C = A^T B (m x m), symmetrised; ns: write the Newton-Schulz polish (3I - C)/2 instead
-  auto gram = [&](PSet A, PSet Bm, bool sym, bool f32, bool ns) {
+  auto gram = [&](PSet A, PSet Bm, bool sym, bool f32, bool ns) -> cudaError_t {
+    if (xs_small) {
+      const XsOperand a = xs_slot(L.oSa, L.oSasc, m, n);       // columns of A
+      const XsOperand bb = xs_slot(L.oSb, L.oSbsc, m, n);      // columns of B
+      cudaError_t r;
+      if ((r = xs_split(A, map1(n), map1(1), a, s))) return r;
+      const bool one = same(A, Bm);
+      if (!one && (r = xs_split(Bm, map1(n), map1(1), bb, s))) return r;
+      if ((r = xs_gemm(a, one ? a : bb, m, m, n, B.Cp.b0, map1(m), map1(1), L.per, gsplit, L.mm,
+                       b.err, s)))
+        return r;
+      k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, B.C, gsplit, m, 0, ns);
+      nl += one ? 3 : 4;
+      return cudaGetLastError();
+    }
     if (f32)
       k_si_gram<float><<<dim3(L.NC, 1, P), 256, 0, s>>>(A, Bm, B.Cp, n, m, sym);
     else
       k_si_gram<double><<<dim3(L.NC, 1, P), 256, 0, s>>>(A, Bm, B.Cp, n, m, sym);
     k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, B.C, L.NC, m, sym, ns);
     nl += 2;
+    return cudaGetLastError();
   };
-  // one CholeskyQR pass in FP32 (Gram and factor), rotation in FP64: dst = src W
-  auto cholqr32 = [&](PSet src, PSet dst, float sh) {
-    gram(src, src, true, true, false);
+  // one CholeskyQR pass with an FP32 factorisation: dst = src W
+  auto cholqr32 = [&](PSet src, PSet dst, float sh) -> cudaError_t {
+    cudaError_t r = gram(src, src, true, true, false);
+    if (r) return r;
     k_si_chol32<<<gz, kCholThreads, chol32_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
-    k_si_rotate<<<grot, 256, 0, s>>>(src, B.W, dst, n, m, 1);
-    nl += 2;
+    nl += 1;
+    return rot(src, B.W, dst, 1);
   };
   // one CholeskyQR pass in FP64 (robust for any conditioning with the shift)
-  auto cholqr64 = [&](PSet src, PSet dst, double sh) {
-    gram(src, src, true, false, false);
+  auto cholqr64 = [&](PSet src, PSet dst, double sh) -> cudaError_t {
+    cudaError_t r = gram(src, src, true, false, false);
+    if (r) return r;
     k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
-    k_si_rotate<<<grot, 256, 0, s>>>(src, B.W, dst, n, m, 1);
-    nl += 2;
+    nl += 1;
+    return rot(src, B.W, dst, 1);
   };
   // FP64 Newton-Schulz step towards orthonormality: dst = src (3I - src^T src) / 2
-  auto polish = [&](PSet src, PSet dst) {
-    gram(src, src, true, false, true);
-    k_si_rotate<<<grot, 256, 0, s>>>(src, B.C, dst, n, m, 0);
-    nl += 1;
+  auto polish = [&](PSet src, PSet dst) -> cudaError_t {
+    cudaError_t r = gram(src, src, true, false, true);
+    return r ? r : rot(src, B.C, dst, 0);
   };
   // dst = orth(src) through tmp (src is overwritten).  Until the first
   // Rayleigh-Ritz step the power-iterated block can be arbitrarily ill
   // conditioned: shifted CholeskyQR3 in FP64.  Afterwards the basis holds Ritz
   // vectors, G X is X Theta up to the residual, its column-scaled Gram matrix is
   // close to I, and two FP32 CholeskyQR passes suffice for the power iteration.
-  auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) {
+  auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) -> cudaError_t {
+    cudaError_t r;
     if (after_rr) {
-      cholqr32(src, tmp, 0.0f);
-      cholqr32(tmp, dst, 0.0f);
-    } else {
-      cholqr64(src, tmp, shift);
-      cholqr64(tmp, src, 0.0);
-      cholqr64(src, dst, 0.0);
+      if ((r = cholqr32(src, tmp, 0.0f))) return r;
+      return cholqr32(tmp, dst, 0.0f);
     }
+    if ((r = cholqr64(src, tmp, shift)) || (r = cholqr64(tmp, src, 0.0))) return r;
+    return cholqr64(src, dst, 0.0);
   };
 
   if ((e = cudaMemsetAsync(B.flag, 0, 4 * sizeof(int), s))) return e;
@@ -1004,8 +1052,8 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   }
   k_si_init<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(X, b.warm, b.has_warm ? 1 : 0, b.kw, n, m);
   nl += 1;
-  cholqr32(X, Z, 0.0f);             // a random start is well conditioned
-  cholqr32(Z, Y, 0.0f);
+  // a random start is well conditioned
+  if ((e = cholqr32(X, Z, 0.0f)) || (e = cholqr32(Z, Y, 0.0f))) return e;
   std::swap(X, Y);
 
   res->converged = false;
@@ -1017,20 +1065,19 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
     if (check) {                    // the Rayleigh-Ritz step needs an FP64-orthonormal basis
-      polish(X, Z);
-      polish(Z, X);
+      if ((e = polish(X, Z)) || (e = polish(Z, X))) return e;
     }
     if ((e = gemm(X, Y))) return e;  // Y = G X
     ++it;
     if (check) {
-      gram(X, Y, false, false, false);   // H = X^T G X
+      if ((e = gram(X, Y, false, false, false))) return e;   // H = X^T G X
       if ((e = launch_jacobi(B.C, m, B.W, B.th, B.flag, B.sweeps, P, s))) return e;
-      k_si_rotate<<<grot, 256, 0, s>>>(X, B.W, Z, n, m, 0);
+      if ((e = rot(X, B.W, Z, 0))) return e;
       std::swap(X, Z);
-      k_si_rotate<<<grot, 256, 0, s>>>(Y, B.W, Z, n, m, 0);
+      if ((e = rot(Y, B.W, Z, 0))) return e;
       std::swap(Y, Z);
       k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, B.sig, b.has_trace ? 1 : 0, n, k);
-      nl += 4;
+      nl += 2;
       ++res->rr;
       if ((e = cudaMemcpy2DAsync(hres.data(), sizeof(double) * k, B.res.at(0), sizeof(double) * L.per,
                                  sizeof(double) * k, P, cudaMemcpyDeviceToHost, s)))
@@ -1061,7 +1108,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
         need = (int)std::ceil(std::log(tol / worst) / std::log(rho)) + 1;
       next_check = it + std::max(1, std::min(need, 8));
     }
-    orth(Y, Z, X, res->rr > 0);     // X = orth(G X)
+    if ((e = orth(Y, Z, X, res->rr > 0))) return e;   // X = orth(G X)
   }
   res->iterations = it;
   if (b.has_trace) {

@@ -72,6 +72,12 @@ struct XsOut {
   long long ssa, ssb;
 };
 
+// One warp per row.  The row maximum is taken on the bit patterns (|x| of a
+// double orders like its bits as an unsigned integer), the scaled row is
+// rounded once to a 6S-bit fixed-point integer (one FP64 multiply and one
+// conversion per element: GB300's FP64 units are slow), and the digits come
+// off that integer from the bottom in balanced form: d_S..d_2 in [-32, 31],
+// then the top digit d_1 = what is left, |d_1| <= 64 because |row| < 2^e.
 template <int S>
 __global__ void __launch_bounds__(256) k_xs_split(PSet src, int R, int K, IdxMap rm, IdxMap km,
                                                   __nv_bfloat16 *dst, int pitch, long long bstride,
@@ -81,31 +87,35 @@ __global__ void __launch_bounds__(256) k_xs_split(PSet src, int R, int K, IdxMap
   if (r >= R) return;
   const double *a = src.at(z);
   const long long ro = map_off(rm, r);
-  double mx = 0.0;
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  unsigned long long mb = 0;
   for (int k = lane; k < K; k += 32) {
-    const double v = fabs(a[ro + map_off(km, k)]);
-    mx = (v != v) ? INFINITY : fmax(mx, v);
+    unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a[ro + map_off(km, k)])) & kAbs;
+    if (u > kInf) u = kInf;                                   // NaN poisons the row like +inf
+    mb = u > mb ? u : mb;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = t > mb ? t : mb;
+  }
+  const double mx = __longlong_as_double(static_cast<long long>(mb));
   int e = 0;
-  const bool finite = isfinite(mx);
-  if (finite && mx > 0.0) (void)frexp(mx, &e);          // mx < 2^e
-  const double inv = ldexp(1.0, -e);
+  const bool finite = mb < kInf;
+  if (finite && mb != 0) (void)frexp(mx, &e);                // mx < 2^e
   if (lane == 0) scale[z * sstride + r] = finite ? ldexp(1.0, e) : NAN;
+  const double up = ldexp(1.0, kXsBits * S - e);             // row -> 6S-bit fixed point
   __nv_bfloat16 *out = dst + z * bstride + (long long)r * pitch;
   const long long plane = (long long)R * pitch;
   for (int k = lane; k < K; k += 32) {
-    double v = finite ? a[ro + map_off(km, k)] * inv : 0.0;   // |v| < 1, exact scaling
-    double unit = 1.0 / 64.0;
+    long long N = finite ? __double2ll_rn(a[ro + map_off(km, k)] * up) : 0;
 #pragma unroll
-    for (int p = 0; p < S; ++p) {
-      const double t = v * 64.0;
-      const double q = rint(t);
-      v = t - q;                                              // exact, |v| <= 1/2
-      out[p * plane + k] = __float2bfloat16_rn((float)(q * unit));   // exact: |q| <= 64
-      unit *= 1.0 / 64.0;
+    for (int p = S - 1; p >= 1; --p) {
+      const long long d = ((N + 32) & 63) - 32;
+      N = (N - d) >> kXsBits;                                 // exact: N - d is a multiple of 64
+      out[p * plane + k] = __float2bfloat16_rn(ldexpf((float)d, -kXsBits * (p + 1)));
     }
+    out[k] = __float2bfloat16_rn(ldexpf((float)N, -kXsBits));
   }
 }
 
