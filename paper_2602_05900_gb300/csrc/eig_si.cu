@@ -175,6 +175,18 @@ __global__ void k_si_unshift(PSet theta, PSet sig, int m) {
   for (int i = threadIdx.x; i < m; i += blockDim.x) theta.at(z)[i] -= sg;
 }
 
+// ks[j] = power of two within a factor 2 of 1 / sqrt(C_jj) (1 if C_jj is not
+// positive and finite): the column scales of a CholeskyQR basis change
+__global__ void k_si_colscale(PSet C, PSet ks, int m) {
+  const int z = blockIdx.z;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double c = C.at(z)[(size_t)j * m + j];
+    int e = 0;
+    if (c > 0.0 && isfinite(c)) (void)frexp(c, &e);
+    ks.at(z)[j] = ldexp(1.0, -(e / 2));
+  }
+}
+
 __global__ void k_si_sum_split(PSet part, PSet out, int S, long long nm) {
   const int z = blockIdx.z;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
@@ -429,15 +441,17 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol(PSet Cin, int m, doubl
 // of kCluster CTAs, laid out as the systolic scheme of Sec. II.B / Fig. 3.
 // The m/2 index pairs of a round are "slots"; slot I holds two whole rows of
 // the matrix (its top and bottom index) and belongs to one CTA (contiguous
-// slots per CTA).  A round: (1) each CTA computes the rotation of its slots
-// from the 2x2 diagonal blocks it holds and broadcasts (p, q, c, s) to the
-// cluster; (2) each CTA applies every column rotation to the rows it holds and
-// its own row rotations, which is M'_{IJ} = J_I^T M_{IJ} J_J for all blocks of
-// its rows (Eq. 6), and rotates its share of the rows of V; (3) rows move to
-// their next slot (tops one slot down, bottoms one slot up, turning at both
-// ends: the round-robin order in which every pair meets once per sweep).
-// Sweeps stop when no pair needs rotating, or after a sweep whose rotated
-// entries were all below 1e-8 relative (quadratic convergence).
+// slots per CTA).  A round: (1) every CTA computes the rotations of all slots
+// from a replicated table of their 2x2 diagonal blocks; (2) each CTA applies
+// every column rotation to the rows it holds and its own row rotations, which
+// is M'_{IJ} = J_I^T M_{IJ} J_J for all blocks of its rows (Eq. 6), and rotates
+// its share of the rows of V; (3) rows move to their next slot (tops one slot
+// down, bottoms one slot up, turning at both ends: the round-robin order in
+// which every pair meets once per sweep), and each moved row writes its entries
+// of the next round's 2x2 blocks into every CTA's table.  One cluster barrier
+// per round; since all CTAs see the same table, the sweep decision needs no
+// exchange.  Sweeps stop when no pair needs rotating, or after a sweep whose
+// rotated entries were all below 1e-8 relative (quadratic convergence).
 __device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &c, double &s) {
   // solve h_pq t^2 + (h_qq - h_pp) t - h_pq = 0 for the smaller root (Golub &
   // Van Loan's symmetric Schur decomposition) on a power-of-two scaled copy:
@@ -480,12 +494,17 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
   double *V = rowsb + (size_t)2 * spc * 2 * m;              // vrows x m
   double *ac = V + (size_t)vrows * m;                       // c of every slot
   double *as = ac + half;                                   // s of every slot
-  int *ap = reinterpret_cast<int *>(as + half);             // p of every slot
+  // angle inputs of every slot, replicated in every CTA, double-buffered by
+  // round parity: [buf][slot][0 = h of the top row's index, 1 = h of the
+  // bottom row's index, 2 = h_pq from the row of the smaller index]
+  double *nd = as + half;
+  double *diag = nd + 2 * 3 * half;                         // m diagonal entries
+  int *ap = reinterpret_cast<int *>(diag + m);              // p of every slot
   int *aq = ap + half;                                      // q of every slot
-  double *diag = reinterpret_cast<double *>(aq + half);   // m diagonal entries (2 half ints: 8-byte aligned)
-  __shared__ int rotated;                        // this CTA's slots needed a rotation
-  __shared__ unsigned int maxrel_bits;           // largest h_pq^2 / (h_pp h_qq) they had
-  __shared__ unsigned int sweep_flags[2 * kCluster];   // per rank: (rotated, maxrel)
+  __shared__ int rotated;
+  __shared__ unsigned int maxrel_bits;
+  auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
+  auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
 
   // round 0 layout: position j holds index j; slot I = positions (I, m-1-I)
   for (int e = threadIdx.x; e < (s1 - s0) * 2 * m; e += blockDim.x) {
@@ -497,25 +516,36 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
     const int rl = e / m, c = e % m;
     V[rl * m + c] = (v0 + rl == c) ? 1.0 : 0.0;
   }
+  for (int sl = threadIdx.x; sl < half; sl += blockDim.x) {
+    const int u = top_index(sl, 0), v = bot_index(sl, 0);
+    const double *C = Cin.at(z);
+    nd[sl * 3 + 0] = C[(size_t)u * m + u];
+    nd[sl * 3 + 1] = C[(size_t)v * m + v];
+    nd[sl * 3 + 2] = C[(size_t)min(u, v) * m + max(u, v)];
+  }
   __syncthreads();
+  // the round-0 inputs are read locally; remote writes only target buffer 1
+  // before the first cluster barrier, so no barrier is needed here
 
   int cur = 0, sweep = 0, r_global = 0;
-  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+  bool stop = false;
+  for (; sweep < kJacobiMaxSweeps && !stop; ++sweep) {
     if (threadIdx.x == 0) {
       rotated = 0;
       maxrel_bits = 0u;
     }
     __syncthreads();
     for (int r = 0; r < m - 1; ++r, ++r_global) {
-      // (1) rotations of own slots; the indices follow the round-robin order
-      for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
-        const int rr = r_global % (m - 1);
-        const int u = (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1);
-        const int v = 1 + (m - 2 - sl + rr) % (m - 1);
-        const double *top = ROW(cur, sl, 0), *bot = ROW(cur, sl, 1);
+      const int rr = r_global % (m - 1), rn = (r_global + 1) % (m - 1);
+      const double *ndc = nd + (r_global & 1) * 3 * half;
+      double *ndn_local = nd + ((r_global + 1) & 1) * 3 * half;
+      // (1) every CTA computes the angles of every slot from the replicated inputs
+      for (int sl = threadIdx.x; sl < half; sl += blockDim.x) {
+        const int u = top_index(sl, rr), v = bot_index(sl, rr);
         const int p = min(u, v), q = max(u, v);
-        const double *rp = (u < v) ? top : bot, *rq = (u < v) ? bot : top;
-        const double hpp = rp[p], hqq = rq[q], hpq = rp[q];
+        const double hpp = (u < v) ? ndc[sl * 3 + 0] : ndc[sl * 3 + 1];
+        const double hqq = (u < v) ? ndc[sl * 3 + 1] : ndc[sl * 3 + 0];
+        const double hpq = ndc[sl * 3 + 2];
         double c = 1.0, sv = 0.0;
         if (hpq * hpq > 1e-30 * fabs(hpp * hqq) && fabs(hpq) > 1e-300) {
           const float den = fabsf((float)hpp * (float)hqq);
@@ -524,18 +554,12 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
           jacobi_angle(hpp, hqq, hpq, c, sv);
           rotated = 1;
         }
-        for (int k = 0; k < kCluster; ++k) {
-          double *rac = cluster.map_shared_rank(ac, k);
-          double *ras = cluster.map_shared_rank(as, k);
-          int *rap = cluster.map_shared_rank(ap, k);
-          int *raq = cluster.map_shared_rank(aq, k);
-          rac[sl] = c;
-          ras[sl] = sv;
-          rap[sl] = p;
-          raq[sl] = q;
-        }
+        ac[sl] = c;
+        as[sl] = sv;
+        ap[sl] = p;
+        aq[sl] = q;
       }
-      cluster.sync();
+      __syncthreads();
       // (2a) every column rotation on the rows this CTA holds
       const int nrow = (s1 - s0) * 2;
       for (int e = threadIdx.x; e < nrow * half; e += blockDim.x) {
@@ -557,15 +581,22 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
       __syncthreads();
       // (2b) row rotation of each own slot, written straight to the next slots;
       // (3) tops move one slot down (slot 1's top to slot 0's bottom), bottoms one
-      // slot up (the last slot's bottom to its own top); slot 0's top stays.
+      // slot up (the last slot's bottom to its own top); slot 0's top stays.  A
+      // row that lands in a slot also publishes that slot's next-round angle
+      // inputs (its diagonal entry, and h_pq if it holds the smaller index) into
+      // every CTA's table.
       double *nx[kCluster];
+      double *ndn[kCluster];
 #pragma unroll
-      for (int k = 0; k < kCluster; ++k) nx[k] = cluster.map_shared_rank(rowsb, k);
+      for (int k = 0; k < kCluster; ++k) {
+        nx[k] = cluster.map_shared_rank(rowsb, k);
+        ndn[k] = cluster.map_shared_rank(ndn_local, k);
+      }
       for (int e = threadIdx.x; e < (s1 - s0) * m; e += blockDim.x) {
         const int sl = s0 + e / m, col = e % m;
         const double *top = ROW(cur, sl, 0), *bot = ROW(cur, sl, 1);
         const int p = ap[sl], q = aq[sl];
-        const int u = (sl == 0) ? 0 : 1 + (sl - 1 + r_global % (m - 1)) % (m - 1);
+        const int u = top_index(sl, rr);
         const bool top_is_p = (u == p);
         const double *rp = top_is_p ? top : bot, *rq = top_is_p ? bot : top;
         const double c = ac[sl], sv = as[sl];
@@ -573,63 +604,49 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
         double nq = sv * rp[col] + c * rq[col];
         if (col == q) np = 0.0;      // the rotated pair is diagonal to rounding
         if (col == p) nq = 0.0;
-        const double ntop = top_is_p ? np : nq, nbot = top_is_p ? nq : np;
-        // destinations in the next buffer
-        int dsl, dtb;
-        if (sl == 0) { dsl = 0; dtb = 0; }               // slot 0's top is fixed
-        else if (sl == 1) { dsl = 0; dtb = 1; }          // -> slot 0 bottom
-        else { dsl = sl - 1; dtb = 0; }
-        {
-          const int own = dsl / spc;
-          double *base = nx[own] + ((((size_t)1 - cur) * spc + (dsl - own * spc)) * 2 + dtb) * m;
-          base[col] = ntop;
-        }
-        if (sl == half - 1) { dsl = sl; dtb = 0; } else { dsl = sl + 1; dtb = 1; }
-        {
-          const int own = dsl / spc;
-          double *base = nx[own] + ((((size_t)1 - cur) * spc + (dsl - own * spc)) * 2 + dtb) * m;
-          base[col] = nbot;
+        const double vals[2] = {top_is_p ? np : nq, top_is_p ? nq : np};   // new top, new bottom
+        int dsl[2], dtb[2];
+        if (sl == 0) { dsl[0] = 0; dtb[0] = 0; }          // slot 0's top is fixed
+        else if (sl == 1) { dsl[0] = 0; dtb[0] = 1; }     // -> slot 0 bottom
+        else { dsl[0] = sl - 1; dtb[0] = 0; }
+        if (sl == half - 1) { dsl[1] = sl; dtb[1] = 0; } else { dsl[1] = sl + 1; dtb[1] = 1; }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          const int own = dsl[w] / spc;
+          double *base = nx[own] + ((((size_t)1 - cur) * spc + (dsl[w] - own * spc)) * 2 + dtb[w]) * m;
+          base[col] = vals[w];
+          const int nu = top_index(dsl[w], rn), nv = bot_index(dsl[w], rn);
+          const int idx = dtb[w] == 0 ? nu : nv, partner = dtb[w] == 0 ? nv : nu;
+          if (col == idx) {
+            for (int k = 0; k < kCluster; ++k) ndn[k][dsl[w] * 3 + dtb[w]] = vals[w];
+          } else if (col == partner && idx < partner) {
+            for (int k = 0; k < kCluster; ++k) ndn[k][dsl[w] * 3 + 2] = vals[w];
+          }
         }
       }
       cluster.sync();
       cur ^= 1;
     }
-    // cluster-wide sweep decision: every CTA publishes its flags into every
-    // CTA's table, then all reduce the same table
-    if (threadIdx.x < kCluster) {
-      unsigned int *tab = cluster.map_shared_rank(sweep_flags, (int)threadIdx.x);
-      tab[2 * rank] = (unsigned)rotated;
-      tab[2 * rank + 1] = maxrel_bits;
-    }
-    cluster.sync();
-    bool any = false;
-    float mx = 0.0f;
-    for (int k = 0; k < kCluster; ++k) {
-      any = any || sweep_flags[2 * k] != 0u;
-      mx = fmaxf(mx, __uint_as_float(sweep_flags[2 * k + 1]));
-    }
-    // quadratic convergence: once every rotated entry was below 1e-8 relative,
-    // what remains after this sweep is at rounding level
-    const bool stop = !any || mx < 1e-16f;
-    cluster.sync();   // the table is read by everyone before the next sweep rewrites it
-    if (stop) {
-      ++sweep;
-      break;
-    }
+    // every CTA saw the same angles: the sweep decision needs no exchange.
+    // Quadratic convergence: once every rotated entry was below 1e-8 relative,
+    // what remains after this sweep is at rounding level.
+    __syncthreads();
+    stop = (rotated == 0) || __uint_as_float(maxrel_bits) < 1e-16f;
+    __syncthreads();
   }
   // diagonal: each CTA knows the index of every row it holds; gather all m values
   {
     const int rr = r_global % (m - 1);
     for (int e = threadIdx.x; e < (s1 - s0) * 2; e += blockDim.x) {
       const int sl = s0 + (e >> 1), tb = e & 1;
-      const int idx = tb == 0 ? ((sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1)) : 1 + (m - 2 - sl + rr) % (m - 1);
+      const int idx = tb == 0 ? top_index(sl, rr) : bot_index(sl, rr);
       const double dv = ROW(cur, sl, tb)[idx];
       for (int k = 0; k < kCluster; ++k) cluster.map_shared_rank(diag, k)[idx] = dv;
     }
   }
   cluster.sync();
   if (threadIdx.x == 0 && rank == 0) {
-    if (sweep >= kJacobiMaxSweeps) atomicExch(flag, 2);
+    if (!stop) atomicExch(flag, 2);
     atomicMax(sweeps, sweep);
   }
   // sort descending (rank of each diagonal entry, ties by index)
@@ -754,7 +771,7 @@ struct Layout {
   // exact-slice operands (BF16 slices and row scales): G, and two general
   // slots for the n x m / m x n / m x m operands of the other products
   int xsp;
-  long long oGs, oGsc, oSa, oSasc, oSb, oSbsc;
+  long long oGs, oGsc, oSa, oSasc, oSb, oSbsc, oKs;
 };
 
 Layout layout(int P, int n, int m) {
@@ -787,6 +804,7 @@ Layout layout(int P, int n, int m) {
   L.oSasc = o; o += up(std::max(n, m));
   L.oSb = o; o += up((sb + 3) / 4);
   L.oSbsc = o; o += up(std::max(n, m));
+  L.oKs = o; o += up(m);
   L.per = o;
   return L;
 }
@@ -818,8 +836,8 @@ bool same(const PSet &a, const PSet &b) { return a.b0 == b.b0 && a.b1 == b.b1 &&
 size_t jacobi_smem(int m) {
   const int half = m / 2;
   const int spc = (half + kCluster - 1) / kCluster, vrows = (m + kCluster - 1) / kCluster;
-  return ((size_t)2 * spc * 2 * m + (size_t)vrows * m + 2 * half + m) * sizeof(double) +
-         (size_t)(2 * half + 2) * sizeof(int) + 64;
+  return ((size_t)2 * spc * 2 * m + (size_t)vrows * m + 2 * half + 6 * half + m) * sizeof(double) +
+         (size_t)(2 * half) * sizeof(int) + 64;
 }
 size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
 size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(float); }
@@ -969,13 +987,23 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     cudaError_t r0 = product(src, dst);
     return r0 ? r0 : add_shift(src, dst);
   };
-  // dst = src W (n x m times m x m, W column-major; tri: W upper triangular)
+  // dst = src W (n x m times m x m, W column-major; tri: W upper triangular).
+  // A CholeskyQR basis change (tri) normalises columns whose lengths can differ
+  // by many orders of magnitude: the exact-slice product then scales column j
+  // of src by a power of two near 1 / |src_j| (and row j of W inversely), so
+  // that the row slicing of src keeps every column's relative accuracy.
   auto rot = [&](PSet src, PSet W, PSet dst, int tri) -> cudaError_t {
     if (xs_small) {
       const XsOperand a = xs_slot(L.oSa, L.oSasc, n, m);       // rows of X
       const XsOperand w = xs_slot(L.oSb, L.oSbsc, m, m);       // columns of W
+      const PSet ks = pset_linear(work + L.oKs, L.per);
       cudaError_t r;
-      if ((r = xs_split(src, map1(1), map1(n), a, s)) || (r = xs_split(W, map1(m), map1(1), w, s)) ||
+      if (tri) {
+        k_si_colscale<<<dim3(1, 1, P), 128, 0, s>>>(B.C, ks, m);
+        nl += 1;
+      }
+      if ((r = xs_split_scaled(src, map1(1), map1(n), ks, tri ? 1 : 0, a, s)) ||
+          (r = xs_split_scaled(W, map1(m), map1(1), ks, tri ? 2 : 0, w, s)) ||
           (r = xs_gemm(a, w, n, m, m, dst.b0, map1(1), map1(n), L.per, 1, 0, b.err, s)))
         return r;
       nl += 3;
@@ -1034,7 +1062,8 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   // Rayleigh-Ritz step the power-iterated block can be arbitrarily ill
   // conditioned: shifted CholeskyQR3 in FP64.  Afterwards the basis holds Ritz
   // vectors, G X is X Theta up to the residual, its column-scaled Gram matrix is
-  // close to I, and two FP32 CholeskyQR passes suffice for the power iteration.
+  // close to I, and two CholeskyQR passes with FP32 factorisations suffice for
+  // the power iteration.
   auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) -> cudaError_t {
     cudaError_t r;
     if (after_rr) {
@@ -1060,7 +1089,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   res->rr = 0;
   res->residual = INFINITY;
   int it = 0;
-  int next_check = 3;
+  int next_check = std::max(2, b.first_check);
   std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);

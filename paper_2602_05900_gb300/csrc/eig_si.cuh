@@ -32,7 +32,8 @@ struct SiBatch {
   int *err;              // device flag set to 2 if a tensor-core wait runs out (xs only)
   PSet trace;            // Tr G of problem z at trace.at(z)[0] (iteration shift)
   bool has_trace;
-  double shift_rel;      // initial shift / Tr G (about the relative accuracy of G)
+  double shift_rel;      // initial shift / Tr G
+  int first_check;       // iteration of the first Rayleigh-Ritz step (>= 2)
 };
 
 // Where a solve leaves its results inside the workspace: Ritz vectors of

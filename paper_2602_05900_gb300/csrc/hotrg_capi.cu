@@ -160,6 +160,7 @@ struct Group {
   double *spectra = nullptr;      // kMaxSteps x (D_cut + 1) per instance
   double *Uprev[2] = {nullptr, nullptr};
   int nprev[2] = {0, 0}, kprev[2] = {0, 0};
+  int iters_prev[2] = {0, 0};     // subspace iterations of the last solve per direction
   TcPath tc;
   std::vector<GroupStep> steps;
 };
@@ -460,7 +461,11 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       sb.trace = PSet{g.scal + 2, g.scal + 3, kScal};
       sb.has_trace = true;
       sb.shift_rel = 0x1.0p-40;
+      // the solve of the last step in this direction took iters_prev
+      // iterations; a Rayleigh-Ritz step costs several iterations, so the
+      // first one is scheduled just before that count
       const int di = ydir ? 1 : 0;
+      sb.first_check = g.iters_prev[di] > 0 ? std::max(3, g.iters_prev[di] - 1) : 3;
       if (g.nprev[di] == n && g.kprev[di] <= m) {
         // the last isometry of this direction starts both sides' iteration
         sb.warm = pset_pairs(g.Uprev[di], g.Uprev[di], g.sUp);
@@ -471,6 +476,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, 80, st, &r, &nl));
       eig_path = 2;
       eig_iters = r.iterations;
+      g.iters_prev[di] = r.converged ? r.iterations : 0;
       eig_res = r.residual;
       ok = r.converged;
     }

@@ -81,16 +81,25 @@ struct XsOut {
 template <int S>
 __global__ void __launch_bounds__(256) k_xs_split(PSet src, int R, int K, IdxMap rm, IdxMap km,
                                                   __nv_bfloat16 *dst, int pitch, long long bstride,
-                                                  double *scale, long long sstride) {
+                                                  double *scale, long long sstride, PSet kscale,
+                                                  int kmode) {
   const int z = blockIdx.z;
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (r >= R) return;
   const double *a = src.at(z);
+  const double *ks = kmode ? kscale.at(z) : nullptr;
   const long long ro = map_off(rm, r);
+  // element k (with the optional power-of-two column factor)
+  auto elem = [&](int k) {
+    const double v = a[ro + map_off(km, k)];
+    if (kmode == 1) return v * ks[k];
+    if (kmode == 2) return v / ks[k];
+    return v;
+  };
   constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
   unsigned long long mb = 0;
   for (int k = lane; k < K; k += 32) {
-    unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a[ro + map_off(km, k)])) & kAbs;
+    unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(elem(k))) & kAbs;
     if (u > kInf) u = kInf;                                   // NaN poisons the row like +inf
     mb = u > mb ? u : mb;
   }
@@ -108,7 +117,7 @@ __global__ void __launch_bounds__(256) k_xs_split(PSet src, int R, int K, IdxMap
   __nv_bfloat16 *out = dst + z * bstride + (long long)r * pitch;
   const long long plane = (long long)R * pitch;
   for (int k = lane; k < K; k += 32) {
-    long long N = finite ? __double2ll_rn(a[ro + map_off(km, k)] * up) : 0;
+    long long N = finite ? __double2ll_rn(elem(k) * up) : 0;
 #pragma unroll
     for (int p = S - 1; p >= 1; --p) {
       const long long d = ((N + 32) & 63) - 32;
@@ -347,6 +356,11 @@ cudaError_t dispatch_xs(const XsOperand &A, const XsOperand &B, int M, int N, in
 }  // namespace
 
 cudaError_t xs_split(PSet src, IdxMap rm, IdxMap km, const XsOperand &d, cudaStream_t s) {
+  return xs_split_scaled(src, rm, km, PSet{nullptr, nullptr, 0}, 0, d, s);
+}
+
+cudaError_t xs_split_scaled(PSet src, IdxMap rm, IdxMap km, PSet kscale, int kmode,
+                            const XsOperand &d, cudaStream_t s) {
   if (d.rows <= 0 || d.K <= 0) return cudaSuccess;
   if (d.S < 1 || d.S > kXsMaxSlices || d.pitch < d.K) return cudaErrorInvalidValue;
   const dim3 g((d.rows + 7) / 8, 1, d.batch < 1 ? 1 : d.batch);
@@ -356,7 +370,7 @@ cudaError_t xs_split(PSet src, IdxMap rm, IdxMap km, const XsOperand &d, cudaStr
 #define XS_SPLIT_CASE(SS)                                                                     \
   case SS:                                                                                    \
     k_xs_split<SS><<<g, 256, 0, s>>>(src, d.rows, d.K, rm, km, dst, d.pitch, d.bstride,       \
-                                     d.scale, d.sstride);                                     \
+                                     d.scale, d.sstride, kscale, kmode);                      \
     break;
     XS_SPLIT_CASE(1) XS_SPLIT_CASE(2) XS_SPLIT_CASE(3) XS_SPLIT_CASE(4)
     XS_SPLIT_CASE(5) XS_SPLIT_CASE(6) XS_SPLIT_CASE(7) XS_SPLIT_CASE(8)

@@ -51,6 +51,14 @@ inline long long xs_elems(int rows, int K, int S) { return (long long)S * rows *
 // Slices row r of instance z, whose element k is src.at(z)[rm(r) + km(k)].
 cudaError_t xs_split(PSet src, IdxMap rm, IdxMap km, const XsOperand &dst, cudaStream_t s);
 
+// The same with element k multiplied (kmode 1) or divided (kmode 2) by
+// kscale.at(z)[k], a power of two (exact).  A product A B^T with A's columns
+// and B's columns scaled inversely is unchanged, but the row slicing then
+// sees balanced rows: used where the columns of A differ by many orders of
+// magnitude (a column-normalising basis change).
+cudaError_t xs_split_scaled(PSet src, IdxMap rm, IdxMap km, PSet kscale, int kmode,
+                            const XsOperand &dst, cudaStream_t s);
+
 // C(m, n) = sum_k A(m, k) B(n, k) in FP64 for every instance z, written to
 // C + z * cstride + cm(m) + cn(n).  The K range is cut into `ksplit` equal
 // parts (each <= kXsMaxK); part p is written at C + p * pstride (the caller
