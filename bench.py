@@ -510,7 +510,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="ising_044_d32", choices=sorted(CONFIGS) + ["sweep256"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6", "bf16xs"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU legs")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

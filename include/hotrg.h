@@ -71,8 +71,18 @@ typedef enum { HOTRG_DIR_X = 0, HOTRG_DIR_Y = 1 } hotrg_dir;
  *                 FP32 accumulation.
  *   HOTRG_BF16X6  three-term BF16 split a = a1 + a2 + a3; the six products
  *                 whose term indices sum to at most 4, FP32 accumulation.
+ *   HOTRG_BF16XS  exact-slice products (see hotrg_dgemm_emu) with S base-64
+ *                 digits (S = 6 unless HOTRG_OPT_XS_DIGITS says otherwise):
+ *                 every operand row is scaled by a power of two and rounded to
+ *                 6S bits, the digit products are exact and their leading sums
+ *                 accumulate exactly on the tensor cores (K split into parts of
+ *                 at most 2336), intermediates are FP64.  About 2^-(6S+1) per
+ *                 term relative to the row maxima; aimed at free energies
+ *                 within 1e-9 of the FP64 result.
  */
-typedef enum { HOTRG_FP64 = 0, HOTRG_TF32 = 1, HOTRG_BF16X3 = 2, HOTRG_BF16X6 = 3 } hotrg_prec;
+typedef enum {
+  HOTRG_FP64 = 0, HOTRG_TF32 = 1, HOTRG_BF16X3 = 2, HOTRG_BF16X6 = 3, HOTRG_BF16XS = 4
+} hotrg_prec;
 
 /* Per-step diagnostics (all gauge-invariant except ln_c, see hotrg_step_info). */
 typedef struct {
@@ -169,9 +179,11 @@ hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
  *       on the BF16 tensor cores as exact-slice FP64-grade GEMMs (eight base-64
  *       digits per operand row, see hotrg_dgemm_emu); 0: FP64 SIMT kernels.
  *       Either way the eigenpairs meet the same residual bound.
+ *   HOTRG_OPT_XS_DIGITS  4..8 (default 6): digits per operand row in the
+ *       HOTRG_BF16XS contraction mode (digit products per K step: S(S+1)/2).
  * Returns HOTRG_EINVAL for an unknown option or value.
  */
-enum { HOTRG_OPT_EIG_TC_PRODUCTS = 0 };
+enum { HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1 };
 hotrg_status hotrg_set_option(hotrg_ctx *ctx, int option, int value);
 
 /*

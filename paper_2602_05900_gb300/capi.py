@@ -20,10 +20,11 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hotrg.h")
 HOTRG_OK, HOTRG_EINVAL, HOTRG_ENOMEM, HOTRG_ECUDA, HOTRG_EEIG, HOTRG_ENONFINITE, \
     HOTRG_ETIMEOUT, HOTRG_ESTATE = range(8)
 DIR_X, DIR_Y = 0, 1
-PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3}
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3, "bf16xs": 4}
 
 
 OPT_EIG_TC_PRODUCTS = 0
+OPT_XS_DIGITS = 1
 
 
 class StepInfo(ctypes.Structure):

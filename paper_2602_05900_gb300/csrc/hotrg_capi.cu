@@ -32,6 +32,7 @@
 #include "common.cuh"
 #include "eig.cuh"
 #include "eig_si.cuh"
+#include "tc_exact.cuh"
 #include "tc_path.cuh"
 
 using namespace hotrg;
@@ -42,6 +43,7 @@ constexpr int kMaxSteps = 256;
 constexpr int kRecord = 8;       // side, eps_L, eps_R, cut_gap, trace_G, ln_c, -, -
 constexpr int kScal = 8;         // logsum, max scratch, tr G_L, tr G_R, trace T, -, -, -
 constexpr int kMaxInstances = 4096;
+constexpr int kXsDigitsMax = 8;  // digits per operand row of the exact-slice contraction mode
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
@@ -162,6 +164,7 @@ struct Group {
   int nprev[2] = {0, 0}, kprev[2] = {0, 0};
   int iters_prev[2] = {0, 0};     // subspace iterations of the last solve per direction
   TcPath tc;
+  XsWork xw{};                    // exact-slice contraction mode scratch
   std::vector<GroupStep> steps;
 };
 
@@ -178,6 +181,7 @@ struct hotrg_ctx {
   std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
   double *si_work = nullptr;                // eigensolver workspace, shared by the groups
   bool eig_tc = true;                       // exact-slice tensor-core products G X
+  int xs_digits = 6;                        // digits of the exact-slice contraction mode
   int *err = nullptr;
   hotrg_status status = HOTRG_OK;
   std::string msg;
@@ -260,11 +264,38 @@ hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
       (s = dalloc(c, &g.records, g.sRec * G)) || (s = dalloc(c, &g.spectra, g.sSpec * G)) ||
       (s = dalloc(c, &g.Uprev[0], g.sUp * G)) || (s = dalloc(c, &g.Uprev[1], g.sUp * G)))
     return s;
-  if (c->prec == HOTRG_FP64) {
+  if (c->prec == HOTRG_FP64 || c->prec == HOTRG_BF16XS) {
     if ((s = dalloc(c, &g.AL, g.sT * G)) || (s = dalloc(c, &g.BL, g.sT * G)) ||
         (s = dalloc(c, &g.AR, g.sT * G)) || (s = dalloc(c, &g.BR, g.sT * G)) ||
         (s = dalloc(c, &g.P, g.sP * G)) || (s = dalloc(c, &g.Q, g.sP * G)))
       return s;
+    if (c->prec == HOTRG_BF16XS) {
+      // largest operands of the step's GEMMs (every dimension <= Dm, D' <= D_cut)
+      const int Dm2 = g.Dm * g.Dm, Dc = g.D_cut;
+      const int shapes[5][3] = {{Dm2, Dm2, Dm2},                   // a2, a3
+                                {g.Dm * Dc, g.Dm * Dm2, g.Dm},     // a5
+                                {Dc * Dm2, Dm2, Dm2},              // a6
+                                {Dc * Dm2, Dc, Dm2},               // a7
+                                {Dm2, Dm2, Dm2}};
+      long long cap[5] = {0, 0, 0, 0, 0};
+      for (auto &sh : shapes) {
+        long long need[5];
+        xs_gemm_needs(sh[0], sh[1], sh[2], kXsDigitsMax, G, need);
+        for (int i = 0; i < 5; ++i) cap[i] = std::max(cap[i], need[i]);
+      }
+      short *sa = nullptr, *sb = nullptr;
+      if ((s = dalloc(c, &sa, cap[0])) || (s = dalloc(c, &sb, cap[1])) ||
+          (s = dalloc(c, &g.xw.sca, cap[2])) || (s = dalloc(c, &g.xw.scb, cap[3])) ||
+          (cap[4] > 0 && (s = dalloc(c, &g.xw.parts, cap[4]))))
+        return s;
+      g.xw.sa = sa;
+      g.xw.sb = sb;
+      g.xw.cap_a = cap[0];
+      g.xw.cap_b = cap[1];
+      g.xw.cap_sa = cap[2];
+      g.xw.cap_sb = cap[3];
+      g.xw.cap_parts = cap[4];
+    }
   } else {
     const int r = g.tc.init(c->prec, g.D0, g.D_cut, G, c->stream, c->err);
     if (r == 2) return fail(c, HOTRG_ENOMEM, "tensor-core operand buffers do not fit");
@@ -274,7 +305,8 @@ hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
 }
 
 bool valid_prec(hotrg_prec p) {
-  return p == HOTRG_FP64 || p == HOTRG_TF32 || p == HOTRG_BF16X3 || p == HOTRG_BF16X6;
+  return p == HOTRG_FP64 || p == HOTRG_TF32 || p == HOTRG_BF16X3 || p == HOTRG_BF16X6 ||
+         p == HOTRG_BF16XS;
 }
 
 // Shared constructor: n instances, T0s[i] of D0s[i]^4 doubles.
@@ -377,7 +409,12 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   pf.flops(HOTRG_ST_PROJ_T, fG * 2.0 * fDn * fDn * fD * fD * fE * fE);
 
   // ---- a2/a3: environments G_L, G_R ([x1][x2][u1][u2], FP64)
-  const bool tc = (c->prec != HOTRG_FP64);
+  const bool tc = (c->prec == HOTRG_TF32 || c->prec == HOTRG_BF16X3 || c->prec == HOTRG_BF16X6);
+  // FP64 SIMT or exact-slice tensor-core GEMM over the same mapped operands
+  auto mgemm = [&](const MappedGemm &mg) -> cudaError_t {
+    if (c->prec == HOTRG_BF16XS) return gemm_xs(mg, c->xs_digits, g.xw, c->err, st);
+    return gemm_f64(mg, st);
+  };
   if (tc) {
     if (g.tc.environment(g.T, g.sT, D, E, sx, sxp, sy, syp, g.GL, g.GR, g.sT, &pf))
       return fail(c, HOTRG_ECUDA, "tensor-core environment chain failed");
@@ -395,7 +432,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     for (const Part &p : parts) {
       MappedGemm m{(int)DE, (int)DE, (int)DE, g.T, p.row, p.red, g.T, p.row, p.red, p.dst, out_m,
                    out_n, G, g.sT, g.sT, g.sT};
-      CK_CUDA(c, gemm_f64(m, st));
+      CK_CUDA(c, mgemm(m));
     }
     pf.launched(HOTRG_ST_ENV, 4);
     pf.end(HOTRG_ST_ENV);
@@ -406,8 +443,8 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.GL, gm, gn, G, g.sT, g.sT, g.sT};
     MappedGemm gr{(int)D2, (int)D2, (int)E2, g.AR, map1(E2), map1(1), g.BR, map1(E2), map1(1),
                   g.GR, gm, gn, G, g.sT, g.sT, g.sT};
-    CK_CUDA(c, gemm_f64(gl, st));
-    CK_CUDA(c, gemm_f64(gr, st));
+    CK_CUDA(c, mgemm(gl));
+    CK_CUDA(c, mgemm(gr));
     pf.launched(HOTRG_ST_GRAM, 2);
   }
   CK_CUDA(c, symmetrize_trace(g.GL, n, g.sT, g.scal + 2, kScal, G, st));
@@ -534,7 +571,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.T, map3(E, E, syp, sy, sxp), map1(sx),
                   g.P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E),
                   G, g.sU, g.sT, g.sP};
-    CK_CUDA(c, gemm_f64(g5, st));
+    CK_CUDA(c, mgemm(g5));
     pf.launched(HOTRG_ST_PROJ_P, 1);
     pf.end(HOTRG_ST_PROJ_P);
     // a6: Q[a][y][y'][x1'][x2'] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
@@ -544,7 +581,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.T, map2(D, sxp, syp), map2(E, sy, sx),
                   g.Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2),
                   G, g.sP, g.sT, g.sP};
-    CK_CUDA(c, gemm_f64(g6, st));
+    CK_CUDA(c, mgemm(g6));
     pf.launched(HOTRG_ST_PROJ_Q, 1);
     pf.end(HOTRG_ST_PROJ_Q);
     // a7: T'[(a,y,y'), b] = sum_{x1',x2'} Q[(a,y,y'),(x1',x2')] U[(x1' x2'), b]
@@ -554,7 +591,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.U, map1(n), map1(1),
                   g.Tn, tm, tn,
                   G, g.sP, g.sU, g.sT};
-    CK_CUDA(c, gemm_f64(g7, st));
+    CK_CUDA(c, mgemm(g7));
     pf.launched(HOTRG_ST_PROJ_T, 1);
     pf.end(HOTRG_ST_PROJ_T);
   }
@@ -706,6 +743,10 @@ hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
     case HOTRG_OPT_EIG_TC_PRODUCTS:
       if (value != 0 && value != 1) return HOTRG_EINVAL;
       c->eig_tc = value != 0;
+      return HOTRG_OK;
+    case HOTRG_OPT_XS_DIGITS:
+      if (value < 4 || value > kXsDigitsMax) return HOTRG_EINVAL;
+      c->xs_digits = value;
       return HOTRG_OK;
   }
   return HOTRG_EINVAL;

@@ -431,3 +431,63 @@ cudaError_t xs_sum_parts(const double *parts, int nparts, long long pstride, int
 }
 
 }  // namespace hotrg
+
+namespace hotrg {
+namespace {
+
+// C(cm(m) + cn(n)) of instance z = sum_p parts[((p * batch + z) * M + m) * N + n]
+__global__ void k_xs_scatter_parts(const double *parts, int nparts, int batch, int M, int N,
+                                   double *C, IdxMap cm, IdxMap cn, long long bC) {
+  const int z = blockIdx.y;
+  const long long mn = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int p = 0; p < nparts; ++p) v += parts[((long long)p * batch + z) * mn + e];
+    const long long m = e / N, n = e % N;
+    C[z * bC + map_off(cm, m) + map_off(cn, n)] = v;
+  }
+}
+
+}  // namespace
+
+void xs_gemm_needs(int M, int N, int K, int S, int batch, long long need[5]) {
+  const int ks = xs_min_split(K);
+  need[0] = xs_elems(M, K, S) * batch;
+  need[1] = xs_elems(N, K, S) * batch;
+  need[2] = (long long)M * batch;
+  need[3] = (long long)N * batch;
+  need[4] = ks > 1 ? (long long)ks * batch * M * N : 0;
+}
+
+cudaError_t gemm_xs(const MappedGemm &g, int S, const XsWork &w, int *err_flag, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  const int batch = g.batch < 1 ? 1 : g.batch;
+  long long need[5];
+  xs_gemm_needs(g.M, g.N, g.K, S, batch, need);
+  if (need[0] > w.cap_a || need[1] > w.cap_b || need[2] > w.cap_sa || need[3] > w.cap_sb ||
+      need[4] > w.cap_parts)
+    return cudaErrorInvalidValue;
+  const long long ea = xs_elems(g.M, g.K, S), eb = xs_elems(g.N, g.K, S);
+  XsOperand a{w.sa, w.sca, g.M, g.K, xs_pitch(g.K), S, batch, ea, g.M};
+  XsOperand b{w.sb, w.scb, g.N, g.K, xs_pitch(g.K), S, batch, eb, g.N};
+  // a batch of instances at stride bA is the PSet "problem z at A + z bA"
+  const PSet pa{const_cast<double *>(g.A), const_cast<double *>(g.A) + g.bA, 2 * g.bA};
+  const PSet pb{const_cast<double *>(g.B), const_cast<double *>(g.B) + g.bB, 2 * g.bB};
+  cudaError_t e;
+  if ((e = xs_split(pa, g.am, g.ak, a, s)) || (e = xs_split(pb, g.bn, g.bk, b, s))) return e;
+  const int ks = xs_min_split(g.K);
+  if (ks == 1) return xs_gemm(a, b, g.M, g.N, g.K, g.C, g.cm, g.cn, g.bC, 1, 0, err_flag, s);
+  const long long mn = (long long)g.M * g.N;
+  if ((e = xs_gemm(a, b, g.M, g.N, g.K, w.parts, map1(g.N), map1(1), mn, ks, mn * batch,
+                   err_flag, s)))
+    return e;
+  long long blocks = (mn + 255) / 256;
+  const long long cap = (152LL * 8 + batch - 1) / batch;
+  if (blocks > cap) blocks = cap;
+  k_xs_scatter_parts<<<dim3((unsigned)(blocks < 1 ? 1 : blocks), batch), 256, 0, s>>>(
+      w.parts, ks, batch, g.M, g.N, g.C, g.cm, g.cn, g.bC);
+  return cudaGetLastError();
+}
+
+}  // namespace hotrg

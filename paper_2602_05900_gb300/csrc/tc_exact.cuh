@@ -76,3 +76,28 @@ cudaError_t xs_sum_parts(const double *parts, int nparts, long long pstride, int
 inline int xs_min_split(int K) { return (K + kXsMaxK - 1) / kXsMaxK; }
 
 }  // namespace hotrg
+
+namespace hotrg {
+
+// Scratch of gemm_xs: slices and row scales of both operands (for all
+// instances of a batch) and the FP64 partial products of a split K.
+struct XsWork {
+  void *sa, *sb;              // BF16 slices
+  double *sca, *scb;          // row scales
+  double *parts;              // K-part results (dense [part][instance][M][N])
+  long long cap_a, cap_b;     // BF16 elements
+  long long cap_sa, cap_sb;   // doubles
+  long long cap_parts;        // doubles
+};
+
+// Elements gemm_xs needs for one GEMM (A slices, B slices, A scales, B
+// scales, parts), for `batch` instances.
+void xs_gemm_needs(int M, int N, int K, int S, int batch, long long need[5]);
+
+// The mapped GEMM of `g` (C(m, n) = sum_k A(m, k) B(n, k) through index maps,
+// batched) as an exact-slice tensor-core GEMM with S digits: the operands are
+// gathered and sliced, K is split into exact parts, the result is written in
+// FP64 through g's output maps.
+cudaError_t gemm_xs(const MappedGemm &g, int S, const XsWork &w, int *err_flag, cudaStream_t s);
+
+}  // namespace hotrg

@@ -67,6 +67,21 @@ def test_mixed_full_job_error_vs_stored_oracle(pkg, name, prec, tol):
     assert err < tol
 
 
+@pytest.mark.parametrize("name,digits,tol", [("ising_044_d32", 6, 1e-10), ("ising_044h_d48", 6, 1e-10),
+                                             ("ising_044h_d48", 5, 1e-9), ("potts3_d64", 6, 1e-10)])
+def test_exact_slice_full_job_vs_stored_oracle(pkg, name, digits, tol):
+    """The exact-slice contraction mode: the 1e-9 free-energy target at D_cut = 48
+    (measured 3e-13 with six digits, 8e-10 with five)."""
+    from paper_2602_05900_gb300.capi import OPT_XS_DIGITS
+    cfg, g = CONFIGS[name], golden(name)
+    with pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, "bf16xs") as h:
+        h.set_option(OPT_XS_DIGITS, digits)
+        h.run(cfg.steps)
+        err = abs(h.ln_z_per_site() / g["ln_z_per_site"] - 1)
+    print(f"{name} bf16xs S={digits}: relative ln Z/N error vs FP64 oracle = {err:.3e}")
+    assert err < tol
+
+
 def run_to_steady(pkg, cfg, prec):
     h = pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, prec)
     d = "x"

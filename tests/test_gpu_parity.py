@@ -18,7 +18,7 @@ from workloads import BETA_C_ISING, BETA_C_POTTS3, random_tensor
 pytestmark = pytest.mark.gpu
 
 GAP_TOL = 1e-9   # steps with a smaller relative gap at the cut are not compared element-wise
-MIXED_TOL = {"tf32": 2e-4, "bf16x3": 5e-5, "bf16x6": 2e-6}
+MIXED_TOL = {"tf32": 2e-4, "bf16x3": 5e-5, "bf16x6": 2e-6, "bf16xs": 1e-10}
 
 
 @pytest.fixture(scope="module")
@@ -119,7 +119,7 @@ def test_fp64_tensor_and_isometry_after_step(pkg):
     assert np.allclose(np.einsum("abyz,a,b->abyz", Tg, sg, sg), Tn, atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "bf16x6", "bf16xs"])
 @pytest.mark.parametrize("D_cut,nsteps", [(8, 14), (16, 12)])
 def test_mixed_precision_vs_oracle(pkg, prec, D_cut, nsteps):
     T0 = pkg.ising_tensor(0.44, 0.01)
@@ -130,7 +130,7 @@ def test_mixed_precision_vs_oracle(pkg, prec, D_cut, nsteps):
     assert err < MIXED_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "bf16xs"])
 def test_mixed_precision_random_tensor(pkg, prec):
     T0 = random_tensor(4, seed=5)
     r = ref.run(T0, 11, 6, first="y")
