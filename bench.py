@@ -297,7 +297,27 @@ def run_ours(args, world, rank, local):
         out["speedup_vs_fp64_gpu"] = round(value / world / v64, 3)
         out["e2e"] = e2e(pkg, cfg, prec, torch)
         out["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
+        out["precision_modes"] = precision_modes(pkg, stream, torch)
     return out
+
+
+def precision_modes(pkg, stream, torch):
+    """Whole 30-step jobs of the D_cut = 48 Ising configuration (beta 0.44,
+    h 0.01) in each contraction arithmetic: relative ln Z/N error against the
+    stored FP64 oracle value and the job's RG-steps/s."""
+    cfg = CONFIGS["ising_044h_d48"]
+    g = golden(cfg.name)
+    res = {}
+    for prec in ("bf16x3", "bf16xs"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lz = full_job_lnz(pkg, cfg, prec, stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[prec] = {"fe_rel_err_vs_fp64_oracle": abs(lz / g["ln_z_per_site"] - 1) if g else None,
+                     "job_rg_steps_per_s": round(cfg.steps / dt, 3)}
+    res["workload"] = f"{cfg.name} ({cfg.steps} steps incl. transients)"
+    return res
 
 
 def e2e(pkg, cfg, prec, torch):
