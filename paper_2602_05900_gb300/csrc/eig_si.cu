@@ -44,6 +44,7 @@ constexpr int kCluster = 8;      // CTAs per Jacobi problem (one thread-block cl
 constexpr int kJacobiMaxSweeps = 40;
 constexpr int kCholThreads = 256;
 constexpr double kXsSmallWork = 32.0 * 1024 * 1024;   // FP64 FMAs of one n x m x m product batch
+constexpr int kSiSmallBatch = 8;      // problems up to which the solve is latency bound
 constexpr float kChol32Retry = 0x1.0p-12f;   // diagonal shift of a retried FP32 CholeskyQR pass
 
 
@@ -1058,15 +1059,20 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     cudaError_t r = gram(src, src, true, false, true);
     return r ? r : rot(src, B.C, dst, 0);
   };
-  // dst = orth(src) through tmp (src is overwritten).  Until the first
-  // Rayleigh-Ritz step the power-iterated block can be arbitrarily ill
-  // conditioned: shifted CholeskyQR3 in FP64.  Afterwards the basis holds Ritz
-  // vectors, G X is X Theta up to the residual, its column-scaled Gram matrix is
-  // close to I, and two CholeskyQR passes with FP32 factorisations suffice for
-  // the power iteration.
+  // dst = orth(src) through tmp (src is overwritten).  After the first
+  // Rayleigh-Ritz step the basis holds Ritz vectors, G X is X Theta up to the
+  // residual, its column-scaled Gram matrix is close to I, and two CholeskyQR
+  // passes with FP32 factorisations suffice for the power iteration.  Before it
+  // the block can be ill conditioned.  Small batches (latency bound: the
+  // single-CTA FP64 factorisation costs more than its iterations save) use the
+  // same two FP32 passes, the first of which retries with a diagonal shift
+  // where the columns are nearly dependent; large batches use shifted
+  // CholeskyQR3 in FP64, which keeps more of the ill-conditioned directions and
+  // saves iterations on their hardest problems.
+  const bool fp64_start = P > kSiSmallBatch;
   auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) -> cudaError_t {
     cudaError_t r;
-    if (after_rr) {
+    if (after_rr || !fp64_start) {
       if ((r = cholqr32(src, tmp, 0.0f))) return r;
       return cholqr32(tmp, dst, 0.0f);
     }
