@@ -33,7 +33,7 @@ struct SiBatch {
   PSet trace;            // Tr G of problem z at trace.at(z)[0] (iteration shift)
   bool has_trace;
   double shift_rel;      // initial shift / Tr G
-  int first_check;       // iteration of the first Rayleigh-Ritz step (>= 2)
+  int first_check;       // expected convergence iteration (first Rayleigh-Ritz step of small batches)
 };
 
 // Where a solve leaves its results inside the workspace: Ritz vectors of
