@@ -1095,7 +1095,9 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   res->rr = 0;
   res->residual = INFINITY;
   int it = 0;
-  int next_check = std::max(2, b.first_check);
+  // With the FP32 start-up a Rayleigh-Ritz step costs several iterations:
+  // the first one goes where the caller expects convergence.
+  int next_check = fp64_start ? 3 : std::max(3, b.first_check);
   std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
