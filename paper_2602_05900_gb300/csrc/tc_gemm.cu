@@ -105,38 +105,51 @@ struct Cfg {
   static constexpr int BM = 128;
   static constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = Tr::kPlanes * (A_BYTES + B_BYTES);
-  static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+  static constexpr int STAGING_BYTES = 4 * 32 * 33 * 4;     // epilogue transpose, per warp 32 x 33
+  static constexpr int STAGES_RAW = (196 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING_BYTES + 1024;
+  static constexpr int TMEM_COLS = 2 * BN;                   // two accumulator buffers
   static_assert(STAGES >= 2, "pipeline needs two stages");
+  static_assert(TMEM_COLS <= 512, "accumulators exceed tensor memory");
 };
 
+// Persistent, warp-specialised: every CTA walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (N tiles fastest, then M tiles, then the
+// instance of the batch).  Warp 0 streams the operand k-blocks of all its
+// tiles through the shared-memory ring without draining it between tiles;
+// warp 1 issues the MMAs of tile i into tensor-memory buffer i & 1; warps 4-7
+// drain buffer i & 1 to global memory while the MMAs of tile i + 1 proceed.
 template <int MODE, int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-              int M, int N, int K, TcEpilogue epi, int *err_flag) {
+              int M, int N, int K, int batch, TcEpilogue epi, int *err_flag) {
   using C = Cfg<MODE, BN>;
   using Tr = typename C::Tr;
   constexpr int STAGES = C::STAGES;
   constexpr uint32_t IDESC = make_idesc(Tr::kTf32, C::BM, BN);
 
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_fail, s_issued, s_consumed;
 
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // N tiles run fastest: the CTAs that share an A tile are launched together and
-  // read it from L2 instead of HBM; grid.z is the instance of the batch
-  const int m0 = blockIdx.y * C::BM, n0 = blockIdx.x * BN;
-  epi.C = static_cast<char *>(epi.C) +
-          blockIdx.z * epi.bstride * (epi.kind == OutKind::F64 ? 8 : (epi.kind == OutKind::F32 ? 4 : 2));
   const int nkb = (K + Tr::kBK - 1) / Tr::kBK;
+  const int ntn = (N + BN - 1) / BN, mtn = (M + C::BM - 1) / C::BM;
+  const long long ntiles = (long long)ntn * mtn * batch;
+  const int esize = epi.kind == OutKind::F64 ? 8 : (epi.kind == OutKind::F32 ? 4 : 2);
 
   auto a_tile = [&](int s, int p) { return smem_base + s * C::STAGE_BYTES + p * C::A_BYTES; };
   auto b_tile = [&](int s, int p) {
     return smem_base + s * C::STAGE_BYTES + Tr::kPlanes * C::A_BYTES + p * C::B_BYTES;
+  };
+  auto tile_coords = [&](long long t, int &n0, int &m0, int &z) {
+    n0 = (int)(t % ntn) * BN;
+    m0 = (int)((t / ntn) % mtn) * C::BM;
+    z = (int)(t / ((long long)ntn * mtn));
   };
 
   if (threadIdx.x == 0) {
@@ -144,16 +157,19 @@ __global__ void __launch_bounds__(128, 1)
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&acc_bar), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), 4);   // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
     s_issued = 0;
     s_consumed = 0;
   }
-  if (warp == 1) {
+  if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
-                 "r"(BN)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -161,107 +177,139 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_base_sh;
+  auto failed = [&]() { return *(volatile int *)&s_fail != 0; };
 
   if (warp == 0 && lane == 0) {
+    // ---- TMA producer: one continuous k-block stream over all own tiles
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
-    int kb = 0;
-    for (; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
-        atomicExch(&s_fail, 1);
-        break;
+    int g = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int n0, m0, z;
+      tile_coords(t, n0, m0, z);
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1;
+        if (failed() || !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
+          atomicExch(&s_fail, 1);
+          ok = false;
+          break;
+        }
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect_tx(fb, C::STAGE_BYTES);
+        for (int p = 0; p < Tr::kPlanes; ++p)
+          tma_load_4d(a_tile(s, p), &ta, fb, kb * Tr::kBK, m0, p, z);
+        for (int p = 0; p < Tr::kPlanes; ++p)
+          tma_load_4d(b_tile(s, p), &tb, fb, kb * Tr::kBK, n0, p, z);
       }
-      const uint32_t fb = smem_u32(&full_bar[s]);
-      mbar_expect_tx(fb, C::STAGE_BYTES);
-      for (int p = 0; p < Tr::kPlanes; ++p)
-        tma_load_4d(a_tile(s, p), &ta, fb, kb * Tr::kBK, m0, p, blockIdx.z);
-      for (int p = 0; p < Tr::kPlanes; ++p)
-        tma_load_4d(b_tile(s, p), &tb, fb, kb * Tr::kBK, n0, p, blockIdx.z);
     }
-    s_issued = kb;
+    s_issued = g;
   } else if (warp == 1 && lane == 0) {
-    int kb = 0;
-    for (; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
+    // ---- MMA issuer: tile i accumulates into tensor-memory buffer i & 1
+    int g = 0, i = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      if (failed() || !mbar_wait(smem_u32(&acc_empty[buf]), ((i >> 1) & 1) ^ 1)) {
         atomicExch(&s_fail, 1);
         break;
       }
       fence_after();
+      const uint32_t dt = tmem + buf * BN;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1;
+        if (failed() || !mbar_wait(smem_u32(&full_bar[s]), ph)) {
+          atomicExch(&s_fail, 1);
+          ok = false;
+          break;
+        }
+        s_consumed = g + 1;
+        fence_after();
 #pragma unroll
-      for (int k = 0; k < Tr::kBK / Tr::kMmaK; ++k) {
+        for (int k = 0; k < Tr::kBK / Tr::kMmaK; ++k) {
 #pragma unroll
-        for (int q = 0; q < Tr::kProducts; ++q) {
-          int pa, pb;
-          Tr::product(q, pa, pb);
-          const uint64_t ad = sw_desc<128>(a_tile(s, pa) + k * 32);
-          const uint64_t bd = sw_desc<128>(b_tile(s, pb) + k * 32);
-          mma_issue<Tr::kTf32>(tmem, ad, bd, IDESC, (kb | k | q) != 0);
+          for (int q = 0; q < Tr::kProducts; ++q) {
+            int pa, pb;
+            Tr::product(q, pa, pb);
+            const uint64_t ad = sw_desc<128>(a_tile(s, pa) + k * 32);
+            const uint64_t bd = sw_desc<128>(b_tile(s, pb) + k * 32);
+            mma_issue<Tr::kTf32>(dt, ad, bd, IDESC, (kb | k | q) != 0);
+          }
+        }
+        mma_commit(smem_u32(&empty_bar[s]));
+      }
+      if (ok) mma_commit(smem_u32(&acc_full[buf]));
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue warps: thread (warp w, lane l) owns accumulator row 32 (w - 4) + l
+    const int ew = warp - 4;
+    float *stage = reinterpret_cast<float *>(smem_raw + (smem_base - smem_u32(smem_raw)) +
+                                             STAGES * C::STAGE_BYTES) + ew * 32 * 33;
+    const uint32_t trow = static_cast<uint32_t>(ew * 32) << 16;
+    int i = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      if (failed() || !mbar_wait(smem_u32(&acc_full[buf]), (i >> 1) & 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      fence_after();
+      int n0, m0, z;
+      tile_coords(t, n0, m0, z);
+      TcEpilogue e = epi;
+      e.C = static_cast<char *>(epi.C) + (long long)z * epi.bstride * esize;
+      const int row = m0 + ew * 32 + lane;
+      const bool rv = row < M;
+      const long long roff = rv ? map_off(e.cm, row) : -1;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        if (n0 + c * 32 >= N) break;
+        uint32_t r[32];
+        tmem_ld32(tmem + trow + buf * BN + c * 32, r);
+        const int col = n0 + c * 32 + lane;
+        const long long coff = (col < N) ? map_off(e.cn, col) : -1;
+        if (!e.transpose) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const long long co = __shfl_sync(0xffffffffu, coff, j);
+            if (rv && co >= 0) store_out(e, roff + co, __uint_as_float(r[j]));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+          __syncwarp();
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const long long ro = __shfl_sync(0xffffffffu, roff, rr);
+            const float v = stage[rr * 33 + lane];
+            if (ro >= 0 && coff >= 0) store_out(e, ro + coff, v);
+          }
+          __syncwarp();
         }
       }
-      mma_commit(smem_u32(&empty_bar[s]));
+      // buffer drained: the MMA warp may reuse it
+      fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
     }
-    s_consumed = kb;
-    mma_commit(smem_u32(&acc_bar));
   }
   __syncwarp();
-
-  // ---- epilogue: thread (warp w, lane l) owns accumulator row 32 w + l
-  const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0);
-  fence_after();
-  if (!acc_ok) atomicExch(&s_fail, 1);
-  const bool ok = acc_ok && (*(volatile int *)&s_fail == 0);
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    const bool rv = row < M;
-    const long long roff = rv ? map_off(epi.cm, row) : -1;
-    // the pipeline buffers are idle now: 32 x 33 floats of staging per warp
-    float *stage = reinterpret_cast<float *>(smem_raw + (smem_base - smem_u32(smem_raw))) + warp * 32 * 33;
-#pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
-      if (n0 + c * 32 >= N) break;
-      uint32_t r[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, r);
-      const int col = n0 + c * 32 + lane;
-      const long long coff = (col < N) ? map_off(epi.cn, col) : -1;
-      if (!epi.transpose) {
-        // lane = row: consecutive lanes store consecutive rows (unit-stride cm)
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const long long co = __shfl_sync(0xffffffffu, coff, j);
-          if (rv && co >= 0) store_out(epi, roff + co, __uint_as_float(r[j]));
-        }
-      } else {
-        // transpose through shared memory: lane = column of row rr
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
-        __syncwarp();
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-          const long long ro = __shfl_sync(0xffffffffu, roff, rr);
-          const float v = stage[rr * 33 + lane];
-          if (ro >= 0 && coff >= 0) store_out(epi, ro + coff, v);
-        }
-        __syncwarp();
-      }
-    }
-  }
 
   fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_fail) atomicExch(err_flag, 2);
     // TMA copies issued but never consumed (only after a timeout): let them land
-    for (int kb = s_consumed; kb < s_issued; ++kb)
-      (void)mbar_wait(smem_u32(&full_bar[kb % STAGES]), (kb / STAGES) & 1);
+    for (int g = s_consumed; g < s_issued; ++g)
+      (void)mbar_wait(smem_u32(&full_bar[g % STAGES]), (g / STAGES) & 1);
   }
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 2) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
                  : "memory");
   }
 }
@@ -299,9 +347,16 @@ cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, i
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((N + BN - 1) / BN, (M + C::BM - 1) / C::BM, batch);
-  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
-  k_tc_gemm<MODE, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, epi, err);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 148;
+  }
+  const long long tiles = (long long)((N + BN - 1) / BN) * ((M + C::BM - 1) / C::BM) * batch;
+  const int grid = (int)(tiles < nsm ? tiles : nsm);
+  k_tc_gemm<MODE, BN><<<grid, 256, C::SMEM, s>>>(ta, tb, M, N, K, batch, epi, err);
   return cudaGetLastError();
 }
 
