@@ -416,8 +416,9 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     return gemm_f64(mg, st);
   };
   if (tc) {
-    if (g.tc.environment(g.T, g.sT, D, E, sx, sxp, sy, syp, g.GL, g.GR, g.sT, &pf))
-      return fail(c, HOTRG_ECUDA, "tensor-core environment chain failed");
+    if (int r = g.tc.environment(g.T, g.sT, D, E, sx, sxp, sy, syp, g.GL, g.GR, g.sT, &pf))
+      return fail(c, HOTRG_ECUDA, std::string("tensor-core environment chain failed: ") +
+                                      cudaGetErrorString(static_cast<cudaError_t>(r)));
   } else {
     // partials written as [x][u][k][k'] for the Gram combine
     const IdxMap out_m = map2(E, E, (long long)D * E2), out_n = map2(E, 1, E2);
@@ -457,7 +458,6 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   int spec_n;
   int eig_path = 0, eig_iters = 0;
   double eig_res = 0.0;
-  bool fallback = false;
   if (n <= g.D_cut) {
     // nothing is cut (U = I); the spectrum of G_L is still recorded
     CK_CUDA(c, identity_isometry(g.U, n, g.sU, G, st));
@@ -527,7 +527,6 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       // library fallback, one environment at a time (the own solver leaves
       // G_L and G_R untouched); vectors overwrite the leading columns of G
       eig_path = 3;
-      fallback = true;
       for (int j = 0; j < G; ++j) {
         if (int r = c->eig.top(g.GL + j * g.sT, n, k, g.wL + j * g.sW, 0))
           return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (left) failed");
@@ -552,7 +551,6 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     g.kprev[di] = Dn;
     spec_n = k;
   }
-  (void)fallback;
   pf.end(HOTRG_ST_EIG);
 
   // ---- a5-a7: projection chain
@@ -561,8 +559,9 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                          : map3(E, E, (long long)Dn * Dn, (long long)E * Dn * Dn, Dn);
   const IdxMap tn = ydir ? map1(E2) : map1(1);
   if (tc) {
-    if (g.tc.project(g.T, g.sT, g.U, g.sU, D, E, Dn, sx, sxp, sy, syp, g.Tn, g.sT, tm, tn, &pf))
-      return fail(c, HOTRG_ECUDA, "tensor-core projection chain failed");
+    if (int r = g.tc.project(g.T, g.sT, g.U, g.sU, D, E, Dn, sx, sxp, sy, syp, g.Tn, g.sT, tm, tn, &pf))
+      return fail(c, HOTRG_ECUDA, std::string("tensor-core projection chain failed: ") +
+                                      cudaGetErrorString(static_cast<cudaError_t>(r)));
   } else {
     // a5: P[a][x1'][y][x2][k] = sum_x1 U[(x1 x2), a] T[x1,x1',y,k]
     pf.begin(HOTRG_ST_PROJ_P);

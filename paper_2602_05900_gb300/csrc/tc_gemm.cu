@@ -105,7 +105,8 @@ struct Cfg {
   static constexpr int BM = 128;
   static constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = Tr::kPlanes * (A_BYTES + B_BYTES);
-  static constexpr int STAGING_BYTES = 4 * 32 * 33 * 4;     // epilogue transpose, per warp 32 x 33
+  static constexpr int EPI_WARPS = 8;                        // two per tensor-memory lane quadrant
+  static constexpr int STAGING_BYTES = EPI_WARPS * 32 * 33 * 4;   // epilogue transpose, 32 x 33 per warp
   static constexpr int STAGES_RAW = (196 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
   static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING_BYTES + 1024;
@@ -118,10 +119,13 @@ struct Cfg {
 // blockIdx.x + gridDim.x, ... (N tiles fastest, then M tiles, then the
 // instance of the batch).  Warp 0 streams the operand k-blocks of all its
 // tiles through the shared-memory ring without draining it between tiles;
-// warp 1 issues the MMAs of tile i into tensor-memory buffer i & 1; warps 4-7
-// drain buffer i & 1 to global memory while the MMAs of tile i + 1 proceed.
+// warp 1 issues the MMAs of tile i into tensor-memory buffer i & 1; warps
+// 4-11 drain buffer i & 1 to global memory while the MMAs of tile i + 1 proceed
+// (warp w reads tensor-memory lanes 32 (w mod 4) .. + 31, the two warps of a
+// quadrant take alternate 32-column chunks: the epilogue is latency bound, so
+// it gets two warps per scheduler).
 template <int MODE, int BN>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(384, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               int M, int N, int K, int batch, TcEpilogue epi, int *err_flag) {
   using C = Cfg<MODE, BN>;
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(256, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
-      mbar_init(smem_u32(&acc_empty[b]), 4);   // one arrival per epilogue warp
+      mbar_init(smem_u32(&acc_empty[b]), C::EPI_WARPS);   // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
@@ -243,11 +247,12 @@ __global__ void __launch_bounds__(256, 1)
       if (ok) mma_commit(smem_u32(&acc_full[buf]));
     }
   } else if (warp >= 4) {
-    // ---- epilogue warps: thread (warp w, lane l) owns accumulator row 32 (w - 4) + l
+    // ---- epilogue warps: thread (warp w, lane l) owns accumulator row 32 (w mod 4) + l
     const int ew = warp - 4;
+    const int quad = warp & 3, half = ew >> 2;
     float *stage = reinterpret_cast<float *>(smem_raw + (smem_base - smem_u32(smem_raw)) +
                                              STAGES * C::STAGE_BYTES) + ew * 32 * 33;
-    const uint32_t trow = static_cast<uint32_t>(ew * 32) << 16;
+    const uint32_t trow = static_cast<uint32_t>(quad * 32) << 16;
     int i = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int buf = i & 1;
@@ -260,11 +265,11 @@ __global__ void __launch_bounds__(256, 1)
       tile_coords(t, n0, m0, z);
       TcEpilogue e = epi;
       e.C = static_cast<char *>(epi.C) + (long long)z * epi.bstride * esize;
-      const int row = m0 + ew * 32 + lane;
+      const int row = m0 + quad * 32 + lane;
       const bool rv = row < M;
       const long long roff = rv ? map_off(e.cm, row) : -1;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = half; c < BN / 32; c += 2) {
         if (n0 + c * 32 >= N) break;
         uint32_t r[32];
         tmem_ld32(tmem + trow + buf * BN + c * 32, r);
@@ -356,7 +361,7 @@ cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, i
   }
   const long long tiles = (long long)((N + BN - 1) / BN) * ((M + C::BM - 1) / C::BM) * batch;
   const int grid = (int)(tiles < nsm ? tiles : nsm);
-  k_tc_gemm<MODE, BN><<<grid, 256, C::SMEM, s>>>(ta, tb, M, N, K, batch, epi, err);
+  k_tc_gemm<MODE, BN><<<grid, 384, C::SMEM, s>>>(ta, tb, M, N, K, batch, epi, err);
   return cudaGetLastError();
 }
 

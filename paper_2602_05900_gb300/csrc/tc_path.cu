@@ -176,12 +176,12 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
   const int DE = D * E, E2 = E * E, D2 = D * D;
   const int p2 = tc_pitch(DE, I.mode);   // a2 operand pitch
   const int p3 = tc_pitch(E2, I.mode);   // a3 operand pitch
-  if ((std::size_t)DE * p2 > I.capT || (std::size_t)D2 * p3 > I.capT) return 1;
+  if ((std::size_t)DE * p2 > I.capT || (std::size_t)D2 * p3 > I.capT) return cudaErrorInvalidValue;
   const IdxMap rows[4] = {map2(E, syp, sx), map2(E, sy, sx), map2(E, syp, sxp), map2(E, sy, sxp)};
   const IdxMap reds[4] = {map2(E, sy, sxp), map2(E, syp, sxp), map2(E, sy, sx), map2(E, syp, sx)};
   hook->begin(HOTRG_ST_PREP);
   for (int i = 0; i < 4; ++i)
-    if (gather(I, T, sT, DE, DE, p2, rows[i], reds[i], I.opT[i]) != cudaSuccess) return 1;
+    if (cudaError_t e_ = gather(I, T, sT, DE, DE, p2, rows[i], reds[i], I.opT[i])) return e_;
   hook->launched(HOTRG_ST_PREP, 4);
   hook->end(HOTRG_ST_PREP);
   hook->begin(HOTRG_ST_ENV);
@@ -190,7 +190,7 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
     TcOperand op = operand(I, I.opT[i], DE, DE, p2, I.sTop);
     TcEpilogue ep = operand_epilogue(I, I.part[i], (long long)D2 * p3,
                                      map2(E, E, (long long)D * p3), map2(E, 1, p3), I.sTop);
-    if (tc_gemm(I.mode, op, op, DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
+    if (cudaError_t e_ = tc_gemm(I.mode, op, op, DE, DE, DE, ep, I.err, I.s)) return e_;
   }
   hook->launched(HOTRG_ST_ENV, 4);
   hook->end(HOTRG_ST_ENV);
@@ -199,9 +199,9 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
   for (int side = 0; side < 2; ++side) {
     TcOperand a = operand(I, I.part[2 * side], D2, E2, p3, I.sTop);
     TcOperand b = operand(I, I.part[2 * side + 1], D2, E2, p3, I.sTop);
-    if (tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(side ? GR : GL, gm, gn, sG), I.err, I.s) !=
-        cudaSuccess)
-      return 1;
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(side ? GR : GL, gm, gn, sG),
+                                 I.err, I.s))
+      return e_;
   }
   hook->launched(HOTRG_ST_GRAM, 2);
   return 0;   // the driver closes the GRAM stage after symmetrising
@@ -216,15 +216,15 @@ int TcPath::project(const double *T, long long sT, const double *U, long long sU
   if ((std::size_t)D * Dn * p5 > I.capT || (std::size_t)D * E2 * p5 > I.capT ||
       (std::size_t)DE * p6 > I.capT || (std::size_t)Dn * p7 > I.capT ||
       (std::size_t)Dn * DE * p6 > I.capP || (std::size_t)Dn * E2 * p7 > I.capP)
-    return 1;
+    return cudaErrorInvalidValue;
   // a1: operands of a5 (U and T views with the x1 axis as K), a6 (T view) and a7 (U^T)
   hook->begin(HOTRG_ST_PREP);
-  if (gather(I, U, sU, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5) != cudaSuccess) return 1;
-  if (gather(I, T, sT, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5) != cudaSuccess)
-    return 1;
-  if (gather(I, T, sT, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6) != cudaSuccess)
-    return 1;
-  if (gather(I, U, sU, Dn, n, p7, map1(n), map1(1), I.opU7) != cudaSuccess) return 1;
+  if (cudaError_t e_ = gather(I, U, sU, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5)) return e_;
+  if (cudaError_t e_ = gather(I, T, sT, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5))
+    return e_;
+  if (cudaError_t e_ = gather(I, T, sT, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6))
+    return e_;
+  if (cudaError_t e_ = gather(I, U, sU, Dn, n, p7, map1(n), map1(1), I.opU7)) return e_;
   hook->launched(HOTRG_ST_PREP, 4);
   hook->end(HOTRG_ST_PREP);
 
@@ -235,7 +235,7 @@ int TcPath::project(const double *T, long long sT, const double *U, long long sU
     const long long ps = (long long)Dn * DE * p6;
     TcEpilogue ep = operand_epilogue(I, I.P, ps, map2(Dn, (long long)DE * p6, E),
                                      map3(E, E, 1, p6, (long long)E * p6), I.sPop);
-    if (tc_gemm(I.mode, a, b, D * Dn, D * E2, D, ep, I.err, I.s) != cudaSuccess) return 1;
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, D * Dn, D * E2, D, ep, I.err, I.s)) return e_;
   }
   hook->launched(HOTRG_ST_PROJ_P, 1);
   hook->end(HOTRG_ST_PROJ_P);
@@ -247,7 +247,7 @@ int TcPath::project(const double *T, long long sT, const double *U, long long sU
     TcEpilogue ep = operand_epilogue(I, I.Q, ps,
                                      map3(E, D, (long long)E * p7, D, (long long)E2 * p7),
                                      map2(D, 1, p7), I.sPop);
-    if (tc_gemm(I.mode, a, b, Dn * DE, DE, DE, ep, I.err, I.s) != cudaSuccess) return 1;
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, Dn * DE, DE, DE, ep, I.err, I.s)) return e_;
   }
   hook->launched(HOTRG_ST_PROJ_Q, 1);
   hook->end(HOTRG_ST_PROJ_Q);
@@ -255,9 +255,9 @@ int TcPath::project(const double *T, long long sT, const double *U, long long sU
   hook->begin(HOTRG_ST_PROJ_T);
   {
     TcOperand a = operand(I, I.Q, Dn * E2, n, p7, I.sPop), b = operand(I, I.opU7, Dn, n, p7, I.sTop);
-    if (tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn, sTout), I.err, I.s) !=
-        cudaSuccess)
-      return 1;
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn, sTout),
+                                 I.err, I.s))
+      return e_;
   }
   hook->launched(HOTRG_ST_PROJ_T, 1);
   hook->end(HOTRG_ST_PROJ_T);

@@ -17,6 +17,7 @@ class TcPath {
   // 0 on success, 1 CUDA error, 2 allocation failure.  err_flag (device int)
   // receives 2 if a kernel's bounded wait runs out.
   int init(hotrg_prec prec, int D0, int D_cut, int G, cudaStream_t s, int *err_flag);
+  // Both chains return 0 or the CUDA error of the failing call.
   // a2 + a3: environments G_L, G_R (FP64, [x1,x2,u1,u2], instance stride sG) of a
   // Y step on the strided view (sx, sxp, sy, syp) of T (instance stride sT) with
   // fused dim D and contracted dim E.
