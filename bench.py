@@ -341,7 +341,7 @@ def e2e(pkg, cfg, prec, torch):
             "note": f"full {cfg.steps}-step job incl. context creation and transient steps"}
 
 
-def cpu_baseline(cfg, budget_s=20.0, max_steps=8):
+def cpu_baseline(cfg, budget_s=20.0, max_steps=64):
     """The FP64 oracle, as it stands, on the host cores: steady-state steps of the
     same workload until about budget_s seconds of CPU work."""
     from oracle import hotrg as ref
@@ -527,7 +527,7 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=120)   # ~1 s timed at D=32: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="ising_044_d32", choices=sorted(CONFIGS) + ["sweep256"])
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6", "bf16xs"])
