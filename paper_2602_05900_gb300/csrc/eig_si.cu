@@ -45,6 +45,7 @@ constexpr int kJacobiMaxSweeps = 40;
 constexpr int kCholThreads = 256;
 constexpr double kXsSmallWork = 32.0 * 1024 * 1024;   // FP64 FMAs of one n x m x m product batch
 constexpr int kSiSmallBatch = 8;      // problems up to which the solve is latency bound
+constexpr double kSiFloorTol = 1e-10;  // residuals accepted once they stop decreasing
 constexpr float kChol32Retry = 0x1.0p-12f;   // diagonal shift of a retried FP32 CholeskyQR pass
 
 
@@ -1099,6 +1100,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   // the first one goes where the caller expects convergence.
   int next_check = fp64_start ? 3 : std::max(3, b.first_check);
   std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
+  double prev_worst = INFINITY;
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
     if (check) {                    // the Rayleigh-Ritz step needs an FP64-orthonormal basis
@@ -1129,10 +1131,16 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       for (double v : hres) worst = std::max(worst, std::isfinite(v) ? v : INFINITY);
       res->residual = worst;
       if (hflag[0]) break;          // factorisation breakdown: let the caller fall back
-      if (worst <= tol) {
+      // Converged at the bound, or at the rounding floor of the products: a
+      // residual below kSiFloorTol that no longer halves between two
+      // Rayleigh-Ritz steps cannot be improved by more iterations (the
+      // exact-slice products reach about 1e-12 relative at n = 4096).
+      const bool stalled = worst <= kSiFloorTol && res->rr >= 2 && worst > 0.5 * prev_worst;
+      if (worst <= tol || stalled) {
         res->converged = true;
         break;
       }
+      prev_worst = worst;
       // Errors in the wanted Ritz pairs shrink by about theta_m / theta_k per
       // iteration: schedule the next check where that predicts convergence.
       double rho = 0.0;
