@@ -305,10 +305,9 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
                                                             int *flag) {
   extern __shared__ float shf[];
   const int ld = m + 1;
-  float *C = shf;                 // m x ld, upper triangle -> R
-  float *Z = shf + m * ld;        // m x ld, R^-1 (upper)
-  float *d = Z + m * ld;          // m
-  float *rinv = d + m;            // m
+  float *C = shf;                 // m x ld: C_hat, updated in place (rows below the step)
+  float *R = shf + m * ld;        // m x ld: the factor R (upper triangle)
+  float *d = R + m * ld;          // m
   const int z = blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -328,6 +327,9 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
         C[a * ld + b] = (float)Cin.at(z)[(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? sh : 0.0f);
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
+    // Right-looking, one barrier per column: every thread reads the pivot and
+    // row j (unchanged during step j), writes its share of R's row j and
+    // updates its share of the trailing block with the unscaled row.
     for (int j = 0; j < m; ++j) {
       const float piv = C[j * ld + j];
       if (!(piv > 0.0f) || !isfinite(piv)) {
@@ -335,15 +337,12 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
         break;
       }
       const float ri = rsqrtf(piv);
-      __syncthreads();
-      for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) C[j * ld + l] *= ri;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        C[j * ld + j] = piv * ri;
-        rinv[j] = ri;
+      for (int l = j + threadIdx.x; l < m; l += blockDim.x) R[j * ld + l] = C[j * ld + l] * ri;
+      const float r2 = ri * ri;
+      for (int a = j + 1 + ty; a < m; a += 16) {
+        const float ca = C[j * ld + a] * r2;
+        for (int b = a + tx; b < m; b += 16) C[a * ld + b] = fmaf(-ca, C[j * ld + b], C[a * ld + b]);
       }
-      for (int a = j + 1 + ty; a < m; a += 16)
-        for (int b = a + tx; b < m; b += 16) C[a * ld + b] = fmaf(-C[j * ld + a], C[j * ld + b], C[a * ld + b]);
       __syncthreads();
     }
     __syncthreads();
@@ -353,20 +352,17 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
     if (threadIdx.x == 0) atomicExch(flag, 1);
     return;
   }
-  for (int a = ty; a < m; a += 16)
-    for (int b = tx; b < m; b += 16) Z[a * ld + b] = (a == b) ? 1.0f : 0.0f;
-  __syncthreads();
-  for (int i = m - 1; i >= 0; --i) {
-    for (int b = i + threadIdx.x; b < m; b += blockDim.x) Z[i * ld + b] *= rinv[i];
-    __syncthreads();
-    for (int a = ty; a < i; a += 16)
-      for (int b = i + tx; b < m; b += 16) Z[a * ld + b] = fmaf(-C[a * ld + i], Z[i * ld + b], Z[a * ld + b]);
-    __syncthreads();
-  }
+  // W = R^-1 diag-scaled: column c of R^-1 by back substitution, one thread per
+  // column (columns are independent; no barriers), W[j + c m] = d_j (R^-1)_jc
   double *W = Wout.at(z);
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int c = e / m, j = e % m;           // W[j + c m]
-    W[e] = (j <= c) ? (double)Z[j * ld + c] * (double)d[j] : 0.0;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    float *zc = C + c;                              // column c of the (now free) C storage
+    for (int i = c; i >= 0; --i) {
+      float acc = (i == c) ? 1.0f : 0.0f;
+      for (int k = i + 1; k <= c; ++k) acc = fmaf(-R[i * ld + k], zc[k * ld], acc);
+      zc[i * ld] = acc / R[i * ld + i];
+    }
+    for (int j = 0; j < m; ++j) W[(size_t)c * m + j] = (j <= c) ? (double)zc[j * ld] * (double)d[j] : 0.0;
   }
 }
 
@@ -842,7 +838,7 @@ size_t jacobi_smem(int m) {
          (size_t)(2 * half) * sizeof(int) + 64;
 }
 size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
-size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(float); }
+size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + m) * sizeof(float); }
 
 cudaError_t set_attrs() {
   static bool done = false;

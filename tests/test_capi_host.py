@@ -97,3 +97,19 @@ def test_batch_argument_validation(lib):
     assert lib.hotrg_batch_size(None, ctypes.byref(n)) == HOTRG_EINVAL
     assert lib.hotrg_batch_step(None, 0) == HOTRG_EINVAL
     assert lib.hotrg_batch_log_z(None, None) == HOTRG_EINVAL
+
+
+def test_option_and_emulated_gemm_argument_validation(lib):
+    from paper_2602_05900_gb300.capi import HOTRG_EINVAL
+    # no context: rejected before any device work
+    assert lib.hotrg_set_option(None, 0, 1) == HOTRG_EINVAL
+    # hotrg_dgemm_emu validates sizes, strides, pointers and digit count first
+    p = ctypes.c_void_p(16)
+    assert lib.hotrg_dgemm_emu(4, 4, 0, p, 4, p, 4, p, 4, 7, None) == HOTRG_EINVAL     # K < 1
+    assert lib.hotrg_dgemm_emu(4, 4, 8, p, 4, p, 8, p, 4, 7, None) == HOTRG_EINVAL     # lda < K
+    assert lib.hotrg_dgemm_emu(4, 4, 8, p, 8, p, 8, p, 2, 7, None) == HOTRG_EINVAL     # ldc < N
+    assert lib.hotrg_dgemm_emu(4, 4, 8, None, 8, p, 8, p, 4, 7, None) == HOTRG_EINVAL  # NULL A
+    assert lib.hotrg_dgemm_emu(4, 4, 8, p, 8, p, 8, p, 4, 3, None) == HOTRG_EINVAL     # digits < 4
+    assert lib.hotrg_dgemm_emu(4, 4, 8, p, 8, p, 8, p, 4, 9, None) == HOTRG_EINVAL     # digits > 8
+    assert lib.hotrg_dgemm_emu(-1, 4, 8, p, 8, p, 8, p, 4, 7, None) == HOTRG_EINVAL
+    assert lib.hotrg_dgemm_emu(0, 4, 8, p, 8, p, 8, p, 4, 7, None) == 0                # empty: nothing to do

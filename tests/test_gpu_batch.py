@@ -110,3 +110,25 @@ def test_batch_rejects_zero_instance_tensor(pkg):
     with pytest.raises(pkg.HotrgError) as e:
         pkg.HotrgBatch([T0, np.zeros_like(T0)], [8, 8], "fp64")
     assert e.value.status == HOTRG_ENONFINITE
+
+
+def test_exact_slice_batch_vs_oracle(pkg, oracle_runs):
+    inst = instances()
+    with pkg.HotrgBatch([gpu_t0(pkg, k, b, h) for k, b, h, _ in inst], [d for *_, d in inst], "bf16xs") as bt:
+        bt.run(12)
+        lz = bt.ln_z_per_site()
+    for i, r in enumerate(oracle_runs):
+        degenerate = min(s.cut_gap for s in r.steps) < GAP_TOL
+        assert abs(lz[i] / r.ln_z_per_site - 1) < (1e-9 if degenerate else 1e-10), i
+
+
+def test_options_are_validated(pkg):
+    from paper_2602_05900_gb300.capi import HOTRG_EINVAL, OPT_EIG_TC_PRODUCTS, OPT_XS_DIGITS
+    with pkg.Hotrg(pkg.ising_tensor(0.44, 0.0), 8, "bf16xs") as h:
+        for opt, val in ((OPT_XS_DIGITS, 3), (OPT_XS_DIGITS, 9), (OPT_EIG_TC_PRODUCTS, 2), (7, 0)):
+            with pytest.raises(pkg.HotrgError) as e:
+                h.set_option(opt, val)
+            assert e.value.status == HOTRG_EINVAL
+        h.set_option(OPT_XS_DIGITS, 4)
+        h.run(8)
+        assert np.isfinite(h.ln_z_per_site())
