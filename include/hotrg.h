@@ -181,9 +181,14 @@ hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
  *       Either way the eigenpairs meet the same residual bound.
  *   HOTRG_OPT_XS_DIGITS  4..8 (default 6): digits per operand row in the
  *       HOTRG_BF16XS contraction mode (digit products per K step: S(S+1)/2).
+ *   HOTRG_OPT_GEMM_AUTOTUNE  1 (default) / 0: the first tensor-core GEMM of
+ *       each shape times every tile width (64, 128, 256 columns) on the
+ *       context's stream and keeps the fastest; 0 uses a fixed rule.  The
+ *       choice never changes results.  Process-wide: it applies to every
+ *       context, and the tuned widths are kept until the process exits.
  * Returns HOTRG_EINVAL for an unknown option or value.
  */
-enum { HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1 };
+enum { HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1, HOTRG_OPT_GEMM_AUTOTUNE = 2 };
 hotrg_status hotrg_set_option(hotrg_ctx *ctx, int option, int value);
 
 /*

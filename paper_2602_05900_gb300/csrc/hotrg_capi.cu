@@ -33,6 +33,7 @@
 #include "eig.cuh"
 #include "eig_si.cuh"
 #include "tc_exact.cuh"
+#include "tc_gemm.cuh"
 #include "tc_path.cuh"
 
 using namespace hotrg;
@@ -746,6 +747,10 @@ hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
     case HOTRG_OPT_XS_DIGITS:
       if (value < 4 || value > kXsDigitsMax) return HOTRG_EINVAL;
       c->xs_digits = value;
+      return HOTRG_OK;
+    case HOTRG_OPT_GEMM_AUTOTUNE:
+      if (value != 0 && value != 1) return HOTRG_EINVAL;
+      tc_set_autotune(value != 0);
       return HOTRG_OK;
   }
   return HOTRG_EINVAL;

@@ -15,7 +15,10 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "tc_gemm.cuh"
 #include "tcgen05.cuh"
@@ -366,17 +369,85 @@ cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, i
 }
 
 template <int MODE>
-cudaError_t dispatch_bn(const TcOperand &A, const TcOperand &B, int M, int N, int K,
-                        const TcEpilogue &epi, int *err, cudaStream_t s) {
+cudaError_t run_bn(int bn, const TcOperand &A, const TcOperand &B, int M, int N, int K,
+                   const TcEpilogue &epi, int *err, cudaStream_t s) {
   const TcMode mode = static_cast<TcMode>(MODE);
-  const int bn = N <= 64 ? 64 : (N <= 128 || MODE != 0 ? 128 : 256);
   CUtensorMap ta, tb;
   if (!make_map(&ta, mode, A, 128) || !make_map(&tb, mode, B, bn)) return cudaErrorInvalidValue;
   const int batch = A.batch < 1 ? 1 : A.batch;
   if (bn == 64) return launch<MODE, 64>(ta, tb, M, N, K, batch, epi, err, s);
   if (bn == 128) return launch<MODE, 128>(ta, tb, M, N, K, batch, epi, err, s);
-  if constexpr (MODE == 0) return launch<MODE, 256>(ta, tb, M, N, K, batch, epi, err, s);
+  if constexpr (MODE == 0) {
+    if (bn == 256) return launch<MODE, 256>(ta, tb, M, N, K, batch, epi, err, s);
+  }
   return cudaErrorInvalidValue;
+}
+
+// Tile-width autotuner: the first GEMM of each shape (mode, M, N, K, batch,
+// output kind and store layout) runs once with every tile width and keeps the
+// fastest (CUDA events on the caller's stream; every width computes the same
+// products in the same order, so the result does not depend on the choice).
+// Shapes met while the stream is being captured into a graph use the cached
+// choice, or the static heuristic if there is none.
+struct TuneKey {
+  int mode, M, N, K, batch, kind, transpose;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(mode, M, N, K, batch, kind, transpose) <
+           std::tie(o.mode, o.M, o.N, o.K, o.batch, o.kind, o.transpose);
+  }
+};
+std::map<TuneKey, int> g_tuned;
+std::mutex g_tune_mu;
+std::atomic<bool> g_autotune{true};
+
+template <int MODE>
+cudaError_t dispatch_bn(const TcOperand &A, const TcOperand &B, int M, int N, int K,
+                        const TcEpilogue &epi, int *err, cudaStream_t s) {
+  const int heuristic = N <= 64 ? 64 : (N <= 128 || MODE != 0 ? 128 : 256);
+  if (!g_autotune.load()) return run_bn<MODE>(heuristic, A, B, M, N, K, epi, err, s);
+  const TuneKey key{MODE, M, N, K, A.batch < 1 ? 1 : A.batch, (int)epi.kind, epi.transpose ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return run_bn<MODE>(it->second, A, B, M, N, K, epi, err, s);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return run_bn<MODE>(heuristic, A, B, M, N, K, epi, err, s);
+  }
+  const int cands[3] = {64, 128, 256};
+  const int ncand = MODE == 0 ? 3 : 2;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    return run_bn<MODE>(heuristic, A, B, M, N, K, epi, err, s);
+  }
+  int best = heuristic;
+  float best_ms = 1e30f;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < ncand && e == cudaSuccess; ++i) {
+    const int bn = cands[i];
+    if ((e = run_bn<MODE>(bn, A, B, M, N, K, epi, err, s))) break;     // warm-up
+    if ((e = cudaEventRecord(ev[0], s)) || (e = run_bn<MODE>(bn, A, B, M, N, K, epi, err, s)) ||
+        (e = cudaEventRecord(ev[1], s)) || (e = cudaEventSynchronize(ev[1])))
+      break;
+    float ms = 0.0f;
+    if ((e = cudaEventElapsedTime(&ms, ev[0], ev[1]))) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+  }
+  return cudaSuccess;   // the last timed launch already wrote the result
 }
 
 }  // namespace
@@ -398,6 +469,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 }  // namespace tc
+
+void tc_set_autotune(bool on) { g_autotune.store(on); }
 
 cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, int N, int K,
                     const TcEpilogue &epi, int *err_flag, cudaStream_t s) {

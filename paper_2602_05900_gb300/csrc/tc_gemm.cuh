@@ -48,10 +48,15 @@ struct TcEpilogue {
 };
 
 // Launches C(M x N) = A(M x K) . B(N x K)^T for every instance of the batch
-// (A.batch == B.batch; grid.z runs over instances); returns a CUDA error code
-// (cudaErrorInvalidValue for unsupported shapes).
+// (A.batch == B.batch; the tiles of all instances form one persistent
+// schedule); returns a CUDA error code (cudaErrorInvalidValue for unsupported
+// shapes).
 cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, int N, int K,
                     const TcEpilogue &epi, int *err_flag, cudaStream_t s);
+
+// Tile-width autotuning of tc_gemm (process-wide, on by default): the first
+// GEMM of each shape times every tile width and keeps the fastest.
+void tc_set_autotune(bool on);
 
 // Number of padded columns an operand row needs so that its byte pitch is a
 // multiple of 16 (the TMA stride rule).
