@@ -128,6 +128,69 @@ __global__ void __launch_bounds__(256) k_xs_split(PSet src, int R, int K, IdxMap
   }
 }
 
+// The same slicing for operands whose rows are contiguous but whose K index is
+// strided (the basis of a rotation X W, column-major X as the A operand): a
+// block stages 32 rows x K (K <= kXsStagedK) through shared memory with loads
+// that run along the rows, then each warp slices its rows along K as above.
+template <int S>
+__global__ void __launch_bounds__(256) k_xs_split_staged(PSet src, int R, int K, IdxMap rm,
+                                                         IdxMap km, __nv_bfloat16 *dst, int pitch,
+                                                         long long bstride, double *scale,
+                                                         long long sstride, PSet kscale, int kmode) {
+  __shared__ double tile[32][kXsStagedK + 1];
+  const int z = blockIdx.z;
+  const int r0 = blockIdx.x * 32;
+  const double *a = src.at(z);
+  const double *ks = kmode ? kscale.at(z) : nullptr;
+  // load: thread t reads row r0 + (t & 31) of column k = t / 32, + 8 per pass
+  for (int e = threadIdx.x; e < 32 * K; e += blockDim.x) {
+    const int rl = e & 31, k = e >> 5, r = r0 + rl;
+    double v = 0.0;
+    if (r < R) {
+      v = a[map_off(rm, r) + map_off(km, k)];
+      if (kmode == 1) v *= ks[k];
+      if (kmode == 2) v /= ks[k];
+    }
+    tile[rl][k] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  for (int rl = threadIdx.x >> 5; rl < 32; rl += blockDim.x >> 5) {
+    const int r = r0 + rl;
+    if (r >= R) break;
+    unsigned long long mb = 0;
+    for (int k = lane; k < K; k += 32) {
+      unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(tile[rl][k])) & kAbs;
+      if (u > kInf) u = kInf;
+      mb = u > mb ? u : mb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = t > mb ? t : mb;
+    }
+    const double mx = __longlong_as_double(static_cast<long long>(mb));
+    int e = 0;
+    const bool finite = mb < kInf;
+    if (finite && mb != 0) (void)frexp(mx, &e);
+    if (lane == 0) scale[z * sstride + r] = finite ? ldexp(1.0, e) : NAN;
+    const double up = ldexp(1.0, kXsBits * S - e);
+    __nv_bfloat16 *out = dst + z * bstride + (long long)r * pitch;
+    const long long plane = (long long)R * pitch;
+    for (int k = lane; k < K; k += 32) {
+      long long N = finite ? __double2ll_rn(tile[rl][k] * up) : 0;
+#pragma unroll
+      for (int p = S - 1; p >= 1; --p) {
+        const long long d = ((N + 32) & 63) - 32;
+        N = (N - d) >> kXsBits;
+        out[p * plane + k] = __float2bfloat16_rn(ldexpf((float)d, -kXsBits * (p + 1)));
+      }
+      out[k] = __float2bfloat16_rn(ldexpf((float)N, -kXsBits));
+    }
+  }
+}
+
 template <int S, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_xs_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
@@ -366,6 +429,20 @@ cudaError_t xs_split_scaled(PSet src, IdxMap rm, IdxMap km, PSet kscale, int kmo
   const dim3 g((d.rows + 7) / 8, 1, d.batch < 1 ? 1 : d.batch);
   if (g.z > 65535u) return cudaErrorInvalidConfiguration;
   __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(d.slices);
+  if (rm.s0 == 1 && rm.n0 >= d.rows && km.s0 != 1 && d.K <= kXsStagedK) {
+    const dim3 gs((d.rows + 31) / 32, 1, d.batch < 1 ? 1 : d.batch);
+    switch (d.S) {
+#define XS_STAGED_CASE(SS)                                                                    \
+  case SS:                                                                                    \
+    k_xs_split_staged<SS><<<gs, 256, 0, s>>>(src, d.rows, d.K, rm, km, dst, d.pitch, d.bstride, \
+                                             d.scale, d.sstride, kscale, kmode);              \
+    break;
+      XS_STAGED_CASE(1) XS_STAGED_CASE(2) XS_STAGED_CASE(3) XS_STAGED_CASE(4)
+      XS_STAGED_CASE(5) XS_STAGED_CASE(6) XS_STAGED_CASE(7) XS_STAGED_CASE(8)
+#undef XS_STAGED_CASE
+    }
+    return cudaGetLastError();
+  }
   switch (d.S) {
 #define XS_SPLIT_CASE(SS)                                                                     \
   case SS:                                                                                    \

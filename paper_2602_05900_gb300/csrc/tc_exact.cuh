@@ -30,6 +30,7 @@ constexpr int kXsBits = 6;        // bits per slice digit
 constexpr int kXsExactDiagonals = 5;  // digit sums d = 2..6 accumulate exactly
 constexpr int kXsMaxK = 2336;     // largest K (multiple of 32) with 7 2^10 K < 2^24
 constexpr int kXsMaxSlices = 8;
+constexpr int kXsStagedK = 128;  // strided-K operands up to this K are sliced through shared memory
 
 // Sliced operand: S planes of rows x pitch BF16 values (plane stride
 // rows * pitch elements, K contiguous) and one power-of-two scale per row, for
