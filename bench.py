@@ -297,6 +297,7 @@ def run_ours(args, world, rank, local):
         out["speedup_vs_fp64_gpu"] = round(value / world / v64, 3)
         out["e2e"] = e2e(pkg, cfg, prec, torch)
         out["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
+        out["cpu_baseline_1_thread"] = cpu_baseline_single_thread(cfg)
         out["precision_modes"] = precision_modes(pkg, stream, torch)
     return out
 
@@ -317,6 +318,20 @@ def precision_modes(pkg, stream, torch):
         res[prec] = {"fe_rel_err_vs_fp64_oracle": abs(lz / g["ln_z_per_site"] - 1) if g else None,
                      "job_rg_steps_per_s": round(cfg.steps / dt, 3)}
     res["workload"] = f"{cfg.name} ({cfg.steps} steps incl. transients)"
+    # configuration 5: q=3 Potts at D_cut = 64, split BF16; device memory of the context
+    p5 = CONFIGS["potts3_d64"]
+    g5 = golden(p5.name)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    t0 = time.perf_counter()
+    with pkg.Hotrg(initial_tensor(pkg, p5), p5.D_cut, p5.precision, stream) as h:
+        free1, _ = torch.cuda.mem_get_info()
+        h.run(p5.steps)
+        lz = h.ln_z_per_site()
+    dt = time.perf_counter() - t0
+    res["potts3_d64_bf16x3"] = {"fe_rel_err_vs_fp64_oracle": abs(lz / g5["ln_z_per_site"] - 1) if g5 else None,
+                                "job_rg_steps_per_s": round(p5.steps / dt, 3),
+                                "context_device_bytes": int(free0 - free1)}
     return res
 
 
@@ -361,9 +376,42 @@ def cpu_baseline(cfg, budget_s=20.0, max_steps=64):
         d = "y" if d == "x" else "x"
         k += 1
     dt = time.perf_counter() - t0
-    return {"value": round(k / dt, 5), "unit": "RG-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": round(k / dt, 5), "unit": "RG-steps/s", "cores": blas_threads(), "kind": "oracle",
+            "blas": blas_name(),
             "sample": f"{k} steady-state steps at D={cfg.D_cut} of {cfg.name} after {n_tr} transient "
-                      f"steps (NumPy/OpenBLAS FP64, {dt:.1f} s)"}
+                      f"steps (NumPy FP64, {dt:.1f} s)"}
+
+
+def blas_name():
+    try:
+        import numpy as np
+        info = np.show_config(mode="dicts")
+        return info.get("Build Dependencies", {}).get("blas", {}).get("name", "unknown")
+    except Exception:
+        return "unknown"
+
+
+def blas_threads():
+    """Threads the oracle's BLAS may use: the *_NUM_THREADS limit, else all cores."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    return os.cpu_count()
+
+
+def cpu_baseline_single_thread(cfg, budget_s=10.0):
+    """The same oracle timing with one BLAS thread (a child process, so that the
+    thread limit is set before NumPy loads its BLAS)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; from workloads import CONFIGS; "
+            "print(json.dumps(bench.cpu_baseline(CONFIGS[%r], budget_s=%r)))") % (ROOT, cfg.name, budget_s)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=budget_s * 10 + 120)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as ex:   # reported, never fatal for the GPU measurement
+        return {"error": str(ex)[:200]}
 
 
 # ----------------------------------------------------------------------------- batched sweep
