@@ -175,9 +175,12 @@ def step_flops(D, E, Dn):
 
 # ----------------------------------------------------------------------------- our arm
 
-def steady_job(pkg, cfg, precision, stream):
+def steady_job(pkg, cfg, precision, stream, autotune=True):
     """A context advanced until Dx = Dy = D_cut; returns (ctx, next direction)."""
     h = pkg.Hotrg(initial_tensor(pkg, cfg), cfg.D_cut, precision, stream)
+    if not autotune:
+        from paper_2602_05900_gb300.capi import OPT_GEMM_AUTOTUNE
+        h.set_option(OPT_GEMM_AUTOTUNE, 0)
     d = "x"
     for _ in range(64):
         dx, dy, _ = h.dims()
@@ -221,7 +224,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    h, d = steady_job(pkg, cfg, prec, stream)
+    h, d = steady_job(pkg, cfg, prec, stream, autotune=not args.no_autotune)
     _, d = time_steps(torch, h, d, args.warmup, stream, flush)
     h.profile_enable(True)
     torch.cuda.synchronize()
@@ -582,6 +585,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU legs")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed GEMM tile widths (profiling: the autotuner's timings are distorted under ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -186,9 +186,18 @@ hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
  *       context's stream and keeps the fastest; 0 uses a fixed rule.  The
  *       choice never changes results.  Process-wide: it applies to every
  *       context, and the tuned widths are kept until the process exits.
+ *   HOTRG_OPT_GRAPHS  1 (default) / 0: the tensor-core contraction chains of
+ *       a step (environment, projection) are captured into CUDA graphs the
+ *       second time a (direction, bond dimensions, buffer) combination occurs
+ *       and replayed afterwards (with the stage profiler on, its events are
+ *       part of the graph).  Needs a non-NULL stream (not the legacy default
+ *       stream); results are bit-identical either way.
  * Returns HOTRG_EINVAL for an unknown option or value.
  */
-enum { HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1, HOTRG_OPT_GEMM_AUTOTUNE = 2 };
+enum {
+  HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1, HOTRG_OPT_GEMM_AUTOTUNE = 2,
+  HOTRG_OPT_GRAPHS = 3
+};
 hotrg_status hotrg_set_option(hotrg_ctx *ctx, int option, int value);
 
 /*

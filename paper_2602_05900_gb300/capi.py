@@ -26,6 +26,7 @@ PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3, "bf16xs": 4}
 OPT_EIG_TC_PRODUCTS = 0
 OPT_XS_DIGITS = 1
 OPT_GEMM_AUTOTUNE = 2
+OPT_GRAPHS = 3
 
 
 class StepInfo(ctypes.Structure):

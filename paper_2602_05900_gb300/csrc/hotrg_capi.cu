@@ -24,7 +24,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <functional>
+#include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -59,6 +63,7 @@ class Profiler : public StageHook {
 
   ~Profiler() {
     for (auto &p : pending_) {
+      if (p.graph_owned) continue;
       cudaEventDestroy(p.b);
       cudaEventDestroy(p.e);
     }
@@ -71,15 +76,47 @@ class Profiler : public StageHook {
   void begin(int stage) override {
     if (!on) return;
     open_[stage] = get();
-    if (open_[stage]) cudaEventRecord(open_[stage], stream);
+    if (open_[stage]) record(open_[stage]);
+  }
+  // inside a capture the event must be an external record node, recorded each
+  // time the graph runs (a plain record would only order the capture)
+  void record(cudaEvent_t e) {
+    if (capture_)
+      cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, stream);
   }
   void end(int stage) override {
     if (!on || !open_[stage]) return;
     cudaEvent_t e = get();
     if (!e) return;
-    cudaEventRecord(e, stream);
-    pending_.push_back({stage, open_[stage], e});
+    record(e);
+    if (capture_) {
+      captured_.push_back({stage, open_[stage], e, true});
+    } else {
+      pending_.push_back({stage, open_[stage], e, false});
+    }
     open_[stage] = nullptr;
+  }
+  // While a graph is captured, the stage events become event-record nodes of
+  // the graph (owned by it, never pooled); each replay queues them for timing.
+  struct Interval {
+    int stage;
+    cudaEvent_t b, e;
+    bool graph_owned;
+  };
+  void begin_capture() {
+    capture_ = true;
+    captured_.clear();
+  }
+  std::vector<Interval> end_capture() {
+    capture_ = false;
+    std::vector<Interval> v;
+    v.swap(captured_);
+    return v;
+  }
+  void replay(const std::vector<Interval> &v) {
+    for (const Interval &i : v) pending_.push_back(i);
   }
   void launched(int stage, int n) override {
     launches_total += n;
@@ -98,24 +135,24 @@ class Profiler : public StageHook {
       cudaError_t r = cudaEventElapsedTime(&ms, p.b, p.e);
       if (r == cudaSuccess) {
         acc.ms[p.stage] += ms;
-        pool_.push_back(p.b);
-        pool_.push_back(p.e);
+        if (!p.graph_owned) {
+          pool_.push_back(p.b);
+          pool_.push_back(p.e);
+        }
       } else if (r == cudaErrorNotReady && !all) {
         keep.push_back(p);
       } else {
         (void)cudaGetLastError();
-        pool_.push_back(p.b);
-        pool_.push_back(p.e);
+        if (!p.graph_owned) {
+          pool_.push_back(p.b);
+          pool_.push_back(p.e);
+        }
       }
     }
     pending_.swap(keep);
   }
 
  private:
-  struct Interval {
-    int stage;
-    cudaEvent_t b, e;
-  };
   cudaEvent_t get() {
     if (!pool_.empty()) {
       cudaEvent_t e = pool_.back();
@@ -129,9 +166,30 @@ class Profiler : public StageHook {
     }
     return e;
   }
-  std::vector<Interval> pending_;
+  std::vector<Interval> pending_, captured_;
   std::vector<cudaEvent_t> pool_;
   cudaEvent_t open_[HOTRG_NSTAGES] = {};
+  bool capture_ = false;
+};
+
+// An instantiated graph of one contraction segment, its kernel count per
+// stage, and the stage events recorded inside it (when it was captured with
+// the profiler on).
+struct SegGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long launches[HOTRG_NSTAGES] = {};
+  std::vector<Profiler::Interval> events;
+};
+
+// Hook used while a segment is captured: stage events go into the graph,
+// launches are counted for the replays.
+struct CaptureHook : StageHook {
+  Profiler *prof;
+  long long per_stage[HOTRG_NSTAGES] = {};
+  explicit CaptureHook(Profiler *p) : prof(p) {}
+  void begin(int stage) override { prof->begin(stage); }
+  void end(int stage) override { prof->end(stage); }
+  void launched(int stage, int n) override { per_stage[stage] += n; }
 };
 
 // Per-step diagnostics that are the same for every instance of a group.
@@ -167,6 +225,21 @@ struct Group {
   TcPath tc;
   XsWork xw{};                    // exact-slice contraction mode scratch
   std::vector<GroupStep> steps;
+  // CUDA graphs of the tensor-core contraction segments, keyed by (segment,
+  // direction, D, E, D', address of T, profiler on): the key fixes every
+  // launch's arguments, and T alternates between two buffers, so a
+  // steady-state run replays two graphs per segment.
+  std::map<std::array<long long, 7>, SegGraph> graphs;
+  std::set<std::array<long long, 7>> seen, nograph;
+  ~Group() {
+    for (auto &kv : graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      for (auto &iv : kv.second.events) {
+        cudaEventDestroy(iv.b);
+        cudaEventDestroy(iv.e);
+      }
+    }
+  }
 };
 
 }  // namespace
@@ -182,6 +255,7 @@ struct hotrg_ctx {
   std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
   double *si_work = nullptr;                // eigensolver workspace, shared by the groups
   bool eig_tc = true;                       // exact-slice tensor-core products G X
+  bool use_graphs = true;                   // replay contraction segments as CUDA graphs
   int xs_digits = 6;                        // digits of the exact-slice contraction mode
   int *err = nullptr;
   hotrg_status status = HOTRG_OK;
@@ -416,8 +490,66 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     if (c->prec == HOTRG_BF16XS) return gemm_xs(mg, c->xs_digits, g.xw, c->err, st);
     return gemm_f64(mg, st);
   };
+  // A tensor-core contraction segment (its launches depend only on the key):
+  // run eagerly the first time (the GEMM autotuner times its shapes then),
+  // captured into a CUDA graph the second time, replayed afterwards.  With the
+  // stage profiler on, the stage events are recorded inside the graph (a
+  // separate graph from the unprofiled one) and timed after each replay.
+  auto run_segment = [&](int seg, const std::function<int(StageHook *)> &body) -> int {
+    if (!c->use_graphs || st == nullptr) return body(&pf);
+    const std::array<long long, 7> key{seg, (long long)dir, D, E, Dn,
+                                       (long long)reinterpret_cast<uintptr_t>(g.T), pf.on ? 1 : 0};
+    auto it = g.graphs.find(key);
+    if (it != g.graphs.end()) {
+      for (int k = 0; k < HOTRG_NSTAGES; ++k)
+        if (it->second.launches[k]) pf.launched(k, (int)it->second.launches[k]);
+      const cudaError_t e = cudaGraphLaunch(it->second.exec, st);
+      if (e == cudaSuccess) pf.replay(it->second.events);
+      return (int)e;
+    }
+    if (g.nograph.count(key) || !g.seen.count(key)) {
+      g.seen.insert(key);
+      return body(&pf);
+    }
+    CaptureHook ch(&pf);
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      g.nograph.insert(key);
+      return body(&pf);
+    }
+    pf.begin_capture();
+    const int r = body(&ch);
+    std::vector<Profiler::Interval> evs = pf.end_capture();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    SegGraph sg;
+    if (r || ec != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&sg.exec, graph, 0ULL) != cudaSuccess) {
+      // not capturable here: nothing of the segment ran; run it eagerly from now on
+      if (graph) cudaGraphDestroy(graph);
+      for (auto &iv : evs) {
+        cudaEventDestroy(iv.b);
+        cudaEventDestroy(iv.e);
+      }
+      (void)cudaGetLastError();
+      g.nograph.insert(key);
+      return body(&pf);
+    }
+    cudaGraphDestroy(graph);
+    std::copy(ch.per_stage, ch.per_stage + HOTRG_NSTAGES, sg.launches);
+    sg.events = std::move(evs);
+    SegGraph &slot = g.graphs[key];
+    slot = std::move(sg);
+    for (int k = 0; k < HOTRG_NSTAGES; ++k)
+      if (slot.launches[k]) pf.launched(k, (int)slot.launches[k]);
+    const cudaError_t e = cudaGraphLaunch(slot.exec, st);
+    if (e == cudaSuccess) pf.replay(slot.events);
+    return (int)e;
+  };
   if (tc) {
-    if (int r = g.tc.environment(g.T, g.sT, D, E, sx, sxp, sy, syp, g.GL, g.GR, g.sT, &pf))
+    if (int r = run_segment(0, [&](StageHook *hook) {
+          return g.tc.environment(g.T, g.sT, D, E, sx, sxp, sy, syp, g.GL, g.GR, g.sT, hook);
+        }))
       return fail(c, HOTRG_ECUDA, std::string("tensor-core environment chain failed: ") +
                                       cudaGetErrorString(static_cast<cudaError_t>(r)));
   } else {
@@ -449,6 +581,8 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     CK_CUDA(c, mgemm(gr));
     pf.launched(HOTRG_ST_GRAM, 2);
   }
+  // the tensor-core chain closed its own Gram stage (it may run as a graph)
+  if (tc) pf.begin(HOTRG_ST_GRAM);
   CK_CUDA(c, symmetrize_trace(g.GL, n, g.sT, g.scal + 2, kScal, G, st));
   CK_CUDA(c, symmetrize_trace(g.GR, n, g.sT, g.scal + 3, kScal, G, st));
   pf.launched(HOTRG_ST_GRAM, 4);
@@ -560,7 +694,10 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                          : map3(E, E, (long long)Dn * Dn, (long long)E * Dn * Dn, Dn);
   const IdxMap tn = ydir ? map1(E2) : map1(1);
   if (tc) {
-    if (int r = g.tc.project(g.T, g.sT, g.U, g.sU, D, E, Dn, sx, sxp, sy, syp, g.Tn, g.sT, tm, tn, &pf))
+    if (int r = run_segment(1, [&](StageHook *hook) {
+          return g.tc.project(g.T, g.sT, g.U, g.sU, D, E, Dn, sx, sxp, sy, syp, g.Tn, g.sT, tm, tn,
+                              hook);
+        }))
       return fail(c, HOTRG_ECUDA, std::string("tensor-core projection chain failed: ") +
                                       cudaGetErrorString(static_cast<cudaError_t>(r)));
   } else {
@@ -751,6 +888,10 @@ hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
     case HOTRG_OPT_GEMM_AUTOTUNE:
       if (value != 0 && value != 1) return HOTRG_EINVAL;
       tc_set_autotune(value != 0);
+      return HOTRG_OK;
+    case HOTRG_OPT_GRAPHS:
+      if (value != 0 && value != 1) return HOTRG_EINVAL;
+      c->use_graphs = value != 0;
       return HOTRG_OK;
   }
   return HOTRG_EINVAL;

@@ -204,7 +204,8 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
       return e_;
   }
   hook->launched(HOTRG_ST_GRAM, 2);
-  return 0;   // the driver closes the GRAM stage after symmetrising
+  hook->end(HOTRG_ST_GRAM);
+  return 0;
 }
 
 int TcPath::project(const double *T, long long sT, const double *U, long long sU, int D, int E,
