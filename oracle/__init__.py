@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for HOTRG on 2D classical lattice models.
+"""FP64 CPU oracle for HOTRG on 2D classical lattice models and quantum chains.
 
 TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, calls, links or
 executes anything in this package: only ``tests/``, ``__graft_entry__.smoke()``
@@ -16,6 +16,9 @@ Contents
 ``brute``       ctypes loader for ``brute_force.c`` (plain C enumeration of all
                 spin configurations of a small torus).
 ``onsager``     Onsager's closed form of the 2D Ising free energy at h = 0.
+``heisenberg``  quantum HOTRG of the spin-1/2 XXZ chain: the Trotterised
+                imaginary-time cell tensor (Sec. II.A-B), dense small-chain
+                references, and the schedule Y steps -> time trace -> X steps.
 ``sampled``     element-by-element evaluation of single-step outputs, for checks
                 at sizes where the full oracle is too slow.
 

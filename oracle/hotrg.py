@@ -55,7 +55,7 @@ import numpy as np
 __all__ = [
     "sqrtm_psd", "initial_tensor", "ising_initial_tensor", "potts_initial_tensor",
     "gram_environments", "eigh_desc", "y_step", "x_step", "HotrgRun", "run",
-    "periodic_trace", "directions",
+    "periodic_trace", "trace_y", "directions",
 ]
 
 
@@ -221,6 +221,21 @@ def x_step(T: np.ndarray, D_cut: int):
 def periodic_trace(T: np.ndarray) -> float:
     """Tr_x Tr_y T = sum_{x,y} T[x,x,y,y] (both directions periodic)."""
     return float(np.einsum("aabb->", T))
+
+
+def trace_y(T: np.ndarray):
+    """Close the y direction: T_x[x, x', 0, 0] = sum_y T[x, x', y, y].
+
+    Returns (T_x / c, c) with c = max |T_x|.  The y legs become trivial (size 1),
+    so every later X step is a plain product of the (Dx x Dx) column matrices
+    and Tr T_x^Lx is the periodic network of Lx columns.
+    """
+    T = np.asarray(T, dtype=np.float64)
+    Tx = np.einsum("abyy->ab", T)[:, :, None, None]
+    c = float(np.max(np.abs(Tx)))
+    if not np.isfinite(c) or c <= 0.0:
+        raise FloatingPointError("traced tensor has no finite nonzero max-norm")
+    return Tx / c, c
 
 
 def directions(nsteps: int, first: str = "x"):
