@@ -117,6 +117,53 @@ hotrg_status hotrg_ising_tensor(double beta, double h, double *T0_out);
 hotrg_status hotrg_potts_tensor(int q, double beta, double *T0_out);
 
 /*
+ * Quantum chains (Sec. II.A: the spin-1/2 antiferromagnetic Heisenberg chain;
+ * Sec. II.B: Z = Tr exp(-beta H) of a quantum chain maps onto a 2D classical
+ * network with an imaginary-time direction, contracted by HOTRG).
+ *
+ * hotrg_xxz_tensor: the cell tensor of the XXZ chain
+ *   H = sum_i Jxy (Sx_i Sx_i+1 + Sy_i Sy_i+1) + Jz Sz_i Sz_i+1
+ * (Jxy = Jz = 1: the antiferromagnetic Heisenberg chain) under the checkerboard
+ * Trotter product Z_M = Tr (exp(-tau H_odd) exp(-tau H_even))^M, beta = M tau.
+ * One cell is two neighbouring sites (e, o) over one period; T0_out receives
+ * 256 doubles, T[x][x'][y][y'] with
+ *   y = 2 s_e + s_o  the two spins at the start of the period, y' at its end
+ *                    (s = 0: Sz = +1/2, s = 1: Sz = -1/2);
+ *   x, x'            the virtual bonds of the odd-bond gates that leave the
+ *                    cell on the left and on the right (dimension 4).
+ * The bond gate g = exp(-tau h) is expanded as sum_k c_k P_k (x) P_k over the
+ * real one-site basis P = (I, sigma_x, [[0,1],[-1,0]], sigma_z); the left site
+ * of a bond carries sqrt|c_k| P_k and the right site sign(c_k) sqrt|c_k| P_k.
+ *   T[x][x'][(e0 o0)][(e2 o2)]
+ *     = sum_{e1,o1} g[(e1 o1)][(e0 o0)] B_x[e2][e1] A_x'[o2][o1]
+ * with A_k = sqrt|c_k| P_k, B_k = sign(c_k) sqrt|c_k| P_k.  Needs tau > 0 and
+ * finite couplings.  Host-only; returns HOTRG_EINVAL on bad arguments.
+ *
+ * Schedule of a finite-temperature run (create with D0 = 4):
+ *   n_t Y steps   compose imaginary time: beta = 2^n_t tau;
+ *   hotrg_trace_y closes the time direction (Z_M is a trace over the
+ *                 time-boundary states);
+ *   n_x X steps   multiply the closed column matrices: a ring of 2^(n_x + 1)
+ *                 sites, the thermodynamic limit as n_x grows.
+ * Then ln Z / N_cells = hotrg_log_z_per_site and the free energy per site is
+ * f = -(ln Z / N_cells) / (2 tau), i.e. hotrg_free_energy with beta = 2 tau.
+ */
+hotrg_status hotrg_xxz_tensor(double Jxy, double Jz, double tau, double *T0_out);
+
+/*
+ * Close the y direction of every instance of the context:
+ *   T[x][x'][0][0] <- sum_y T[x][x'][y][y]   (Dy becomes 1),
+ * then the max-norm rescale; ln(c) enters the log-sum with the weight 2^-n of
+ * the n steps taken so far (the traced tensor still stands for 2^n sites).  It
+ * is not a step: hotrg_dims' step count and the step records are unchanged.
+ * Later X steps have trivial fused legs (nothing is cut) and multiply the
+ * Dx x Dx column matrices, on the FP64 GEMMs in every precision mode.
+ * Synchronises the stream.  Errors: HOTRG_EINVAL (NULL), a sticky context
+ * error, HOTRG_ENONFINITE if the traced tensor is zero or not finite.
+ */
+hotrg_status hotrg_trace_y(hotrg_ctx *ctx);
+
+/*
  * Create a context holding T0 (host, D0^4 doubles, [x,x',y,y'] row-major,
  * borrowed and copied) scaled by its max-norm, ready for steps with cut D_cut.
  * stream: a cudaStream_t (NULL = the legacy default stream); the context

@@ -63,6 +63,8 @@ _SIGS = {
     "hotrg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hotrg_ising_tensor": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _dp]),
     "hotrg_potts_tensor": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _dp]),
+    "hotrg_xxz_tensor": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]),
+    "hotrg_trace_y": (ctypes.c_int, [ctypes.c_void_p]),
     "hotrg_create": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "hotrg_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -145,6 +147,15 @@ def potts_tensor(q: int, beta: float) -> np.ndarray:
     return out
 
 
+def xxz_tensor(Jxy: float, Jz: float, tau: float) -> np.ndarray:
+    """Cell tensor (4, 4, 4, 4) of the Trotterised XXZ chain (two sites, one period)."""
+    out = np.zeros((4, 4, 4, 4))
+    s = load().hotrg_xxz_tensor(Jxy, Jz, tau, _ptr(out))
+    if s:
+        raise HotrgError(s, "hotrg_xxz_tensor rejected its arguments")
+    return out
+
+
 class Hotrg:
     """One HOTRG instance on the GPU (owns a ``hotrg_ctx``)."""
 
@@ -174,6 +185,20 @@ class Hotrg:
     def run(self, nsteps: int, first: str = "x"):
         for i in range(nsteps):
             self.step(first if i % 2 == 0 else ("y" if first == "x" else "x"))
+        return self
+
+    def trace_y(self):
+        """Close the y legs (T[x,x'] = sum_y T[x,x',y,y]) of every instance."""
+        self._check(load().hotrg_trace_y(self._h), "hotrg_trace_y")
+        return self
+
+    def run_quantum(self, n_time: int, n_space: int):
+        """n_time Y steps (beta = 2^n_time tau), the time trace, n_space X steps."""
+        for _ in range(n_time):
+            self.step("y")
+        self.trace_y()
+        for _ in range(n_space):
+            self.step("x")
         return self
 
     def ln_z_per_site(self) -> float:
@@ -294,6 +319,8 @@ class HotrgBatch:
                     "hotrg_batch_step")
 
     run = Hotrg.run
+    trace_y = Hotrg.trace_y
+    run_quantum = Hotrg.run_quantum
 
     def size(self) -> int:
         n = ctypes.c_int()

@@ -89,6 +89,9 @@ cudaError_t maxabs_scale_log(double *T, long long count, long long sT, double *s
                              int batch, cudaStream_t s);
 cudaError_t periodic_trace(const double *T, int Dx, int Dy, long long sT, double *out,
                            long long sOut, int batch, cudaStream_t s);
+// Tx[x][x'] = sum_y T[x][x'][y][y] (Tx and T distinct buffers, same stride sT).
+cudaError_t trace_y(const double *T, double *Tx, int Dx, int Dy, long long sT, int batch,
+                    cudaStream_t s);
 
 // Device-side choice of the environment side and assembly of U (sign-fixed
 // leading eigenvectors) plus the step record, for every instance i: its left

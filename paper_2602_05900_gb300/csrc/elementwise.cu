@@ -122,6 +122,17 @@ __global__ void k_periodic_trace(const double *T, int Dx, int Dy, long long sT, 
   if (threadIdx.x == 0) out[blockIdx.x * sOut] = v;
 }
 
+// Tx[x][x'] = sum_y T[x][x'][y][y]: one thread per output element of every
+// instance (grid.y); the Dy summands of an element lie Dy + 1 apart.
+__global__ void k_trace_y(const double *T, double *Tx, int Dx, int Dy, long long sT) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Dx * Dx) return;
+  const double *t = T + blockIdx.y * sT + (long long)e * Dy * Dy;
+  double v = 0.0;
+  for (int y = 0; y < Dy; ++y) v += t[y * (Dy + 1)];
+  Tx[blockIdx.y * sT + e] = v;
+}
+
 // grid (kept column a, instance).  Every block recomputes the side choice from
 // the eigenvalues (a few dozen adds), so no separate launch or host round trip
 // is needed; block (0, i) also writes instance i's record and spectrum.
@@ -249,6 +260,13 @@ cudaError_t maxabs_scale_log(double *T, long long count, long long sT, double *s
 cudaError_t periodic_trace(const double *T, int Dx, int Dy, long long sT, double *out,
                            long long sOut, int batch, cudaStream_t s) {
   k_periodic_trace<<<batch, 1024, 0, s>>>(T, Dx, Dy, sT, out, sOut);
+  return cudaGetLastError();
+}
+
+cudaError_t trace_y(const double *T, double *Tx, int Dx, int Dy, long long sT, int batch,
+                    cudaStream_t s) {
+  const int n = Dx * Dx;
+  k_trace_y<<<dim3((n + 255) / 256, batch), 256, 0, s>>>(T, Tx, Dx, Dy, sT);
   return cudaGetLastError();
 }
 

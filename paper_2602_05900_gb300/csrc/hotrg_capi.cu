@@ -46,7 +46,7 @@ namespace {
 
 constexpr int kMaxSteps = 256;
 constexpr int kRecord = 8;       // side, eps_L, eps_R, cut_gap, trace_G, ln_c, -, -
-constexpr int kScal = 8;         // logsum, max scratch, tr G_L, tr G_R, trace T, -, -, -
+constexpr int kScal = 8;         // logsum, max scratch, tr G_L, tr G_R, trace T, ln c of trace_y, -, -
 constexpr int kMaxInstances = 4096;
 constexpr int kXsDigitsMax = 8;  // digits per operand row of the exact-slice contraction mode
 
@@ -216,6 +216,10 @@ struct Group {
   double *GL = nullptr, *GR = nullptr;
   double *wL = nullptr, *wR = nullptr;
   double *U = nullptr, *P = nullptr, *Q = nullptr;
+  // tensor-core modes: FP64 partials and P, Q of the steps with D = 1 (each
+  // Dm^2 per instance at stride sC1; the full-size buffers above stay unset)
+  double *c1 = nullptr;
+  long long sC1 = 0;
   double *scal = nullptr;         // kScal per instance
   double *records = nullptr;      // kMaxSteps x kRecord per instance
   double *spectra = nullptr;      // kMaxSteps x (D_cut + 1) per instance
@@ -372,6 +376,8 @@ hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
       g.xw.cap_parts = cap[4];
     }
   } else {
+    g.sC1 = round_up(nmax, 32);
+    if ((s = dalloc(c, &g.c1, 6 * g.sC1 * G))) return s;
     const int r = g.tc.init(c->prec, g.D0, g.D_cut, G, c->stream, c->err);
     if (r == 2) return fail(c, HOTRG_ENOMEM, "tensor-core operand buffers do not fit");
     if (r) return fail(c, HOTRG_ECUDA, "tensor-core path initialisation failed");
@@ -484,10 +490,24 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   pf.flops(HOTRG_ST_PROJ_T, fG * 2.0 * fDn * fDn * fD * fD * fE * fE);
 
   // ---- a2/a3: environments G_L, G_R ([x1][x2][u1][u2], FP64)
-  const bool tc = (c->prec == HOTRG_TF32 || c->prec == HOTRG_BF16X3 || c->prec == HOTRG_BF16X6);
+  // A step whose fused legs are trivial (D = 1: X steps after the y legs were
+  // closed by a trace) multiplies Dx x Dx column matrices, E^3 flops: it runs
+  // on the FP64 SIMT GEMMs in every precision mode.
+  const bool tc = D > 1 &&
+                  (c->prec == HOTRG_TF32 || c->prec == HOTRG_BF16X3 || c->prec == HOTRG_BF16X6);
+  // FP64 partials and projection intermediates: the full-size buffers, or in
+  // the tensor-core modes (D = 1 only) the small ones
+  double *AL = g.AL, *BL = g.BL, *AR = g.AR, *BR = g.BR, *P = g.P, *Q = g.Q;
+  long long sPart = g.sT, sPQ = g.sP;
+  if (!AL) {
+    const long long b = g.sC1 * G;
+    AL = g.c1, BL = g.c1 + b, AR = g.c1 + 2 * b, BR = g.c1 + 3 * b, P = g.c1 + 4 * b,
+    Q = g.c1 + 5 * b;
+    sPart = sPQ = g.sC1;
+  }
   // FP64 SIMT or exact-slice tensor-core GEMM over the same mapped operands
   auto mgemm = [&](const MappedGemm &mg) -> cudaError_t {
-    if (c->prec == HOTRG_BF16XS) return gemm_xs(mg, c->xs_digits, g.xw, c->err, st);
+    if (c->prec == HOTRG_BF16XS && D > 1) return gemm_xs(mg, c->xs_digits, g.xw, c->err, st);
     return gemm_f64(mg, st);
   };
   // A tensor-core contraction segment (its launches depend only on the key):
@@ -557,15 +577,15 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     const IdxMap out_m = map2(E, E, (long long)D * E2), out_n = map2(E, 1, E2);
     struct Part { double *dst; IdxMap row, red; };
     const Part parts[4] = {
-        {g.AL, map2(E, syp, sx), map2(E, sy, sxp)},    // A_L[x1,k,u1,k']: sum over (x1', y)
-        {g.BL, map2(E, sy, sx), map2(E, syp, sxp)},    // B_L[x2,k,u2,k']: sum over (x2', y')
-        {g.AR, map2(E, syp, sxp), map2(E, sy, sx)},    // A_R[x1',k,u1',k']: sum over (x1, y)
-        {g.BR, map2(E, sy, sxp), map2(E, syp, sx)},    // B_R[x2',k,u2',k']: sum over (x2, y')
+        {AL, map2(E, syp, sx), map2(E, sy, sxp)},    // A_L[x1,k,u1,k']: sum over (x1', y)
+        {BL, map2(E, sy, sx), map2(E, syp, sxp)},    // B_L[x2,k,u2,k']: sum over (x2', y')
+        {AR, map2(E, syp, sxp), map2(E, sy, sx)},    // A_R[x1',k,u1',k']: sum over (x1, y)
+        {BR, map2(E, sy, sxp), map2(E, syp, sx)},    // B_R[x2',k,u2',k']: sum over (x2, y')
     };
     pf.begin(HOTRG_ST_ENV);
     for (const Part &p : parts) {
       MappedGemm m{(int)DE, (int)DE, (int)DE, g.T, p.row, p.red, g.T, p.row, p.red, p.dst, out_m,
-                   out_n, G, g.sT, g.sT, g.sT};
+                   out_n, G, g.sT, g.sT, sPart};
       CK_CUDA(c, mgemm(m));
     }
     pf.launched(HOTRG_ST_ENV, 4);
@@ -573,10 +593,10 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     // G[x1,x2,u1,u2] = sum_{k,k'} A[x1,u1,k,k'] B[x2,u2,k,k']
     pf.begin(HOTRG_ST_GRAM);
     const IdxMap gm = map2(D, D, D2 * D), gn = map2(D, 1, D2);
-    MappedGemm gl{(int)D2, (int)D2, (int)E2, g.AL, map1(E2), map1(1), g.BL, map1(E2), map1(1),
-                  g.GL, gm, gn, G, g.sT, g.sT, g.sT};
-    MappedGemm gr{(int)D2, (int)D2, (int)E2, g.AR, map1(E2), map1(1), g.BR, map1(E2), map1(1),
-                  g.GR, gm, gn, G, g.sT, g.sT, g.sT};
+    MappedGemm gl{(int)D2, (int)D2, (int)E2, AL, map1(E2), map1(1), BL, map1(E2), map1(1),
+                  g.GL, gm, gn, G, sPart, sPart, g.sT};
+    MappedGemm gr{(int)D2, (int)D2, (int)E2, AR, map1(E2), map1(1), BR, map1(E2), map1(1),
+                  g.GR, gm, gn, G, sPart, sPart, g.sT};
     CK_CUDA(c, mgemm(gl));
     CK_CUDA(c, mgemm(gr));
     pf.launched(HOTRG_ST_GRAM, 2);
@@ -706,28 +726,28 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     MappedGemm g5{(int)(D * Dn), (int)(D * E2), D,
                   g.U, map2(Dn, n, 1), map1(D),
                   g.T, map3(E, E, syp, sy, sxp), map1(sx),
-                  g.P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E),
-                  G, g.sU, g.sT, g.sP};
+                  P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E),
+                  G, g.sU, g.sT, sPQ};
     CK_CUDA(c, mgemm(g5));
     pf.launched(HOTRG_ST_PROJ_P, 1);
     pf.end(HOTRG_ST_PROJ_P);
     // a6: Q[a][y][y'][x1'][x2'] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
     pf.begin(HOTRG_ST_PROJ_Q);
     MappedGemm g6{(int)(Dn * DE), (int)DE, (int)DE,
-                  g.P, map1(DE), map1(1),
+                  P, map1(DE), map1(1),
                   g.T, map2(D, sxp, syp), map2(E, sy, sx),
-                  g.Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2),
-                  G, g.sP, g.sT, g.sP};
+                  Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2),
+                  G, sPQ, g.sT, sPQ};
     CK_CUDA(c, mgemm(g6));
     pf.launched(HOTRG_ST_PROJ_Q, 1);
     pf.end(HOTRG_ST_PROJ_Q);
     // a7: T'[(a,y,y'), b] = sum_{x1',x2'} Q[(a,y,y'),(x1',x2')] U[(x1' x2'), b]
     pf.begin(HOTRG_ST_PROJ_T);
     MappedGemm g7{(int)(Dn * E2), Dn, (int)D2,
-                  g.Q, map1(D2), map1(1),
+                  Q, map1(D2), map1(1),
                   g.U, map1(n), map1(1),
                   g.Tn, tm, tn,
-                  G, g.sP, g.sU, g.sT};
+                  G, sPQ, g.sU, g.sT};
     CK_CUDA(c, mgemm(g7));
     pf.launched(HOTRG_ST_PROJ_T, 1);
     pf.end(HOTRG_ST_PROJ_T);
@@ -838,6 +858,44 @@ hotrg_status hotrg_potts_tensor(int q, double beta, double *T0_out) {
   return HOTRG_OK;
 }
 
+hotrg_status hotrg_xxz_tensor(double Jxy, double Jz, double tau, double *T0_out) {
+  if (!T0_out || !(tau > 0.0) || !isfinite(tau) || !isfinite(Jxy) || !isfinite(Jz))
+    return HOTRG_EINVAL;
+  // gate g = exp(-tau h) from the spectrum of h: |uu>, |dd> -> Jz/4,
+  // (|ud> + |du>)/sqrt2 -> Jxy/2 - Jz/4, (|ud> - |du>)/sqrt2 -> -Jxy/2 - Jz/4
+  const double p = exp(-0.25 * tau * Jz);
+  const double es = exp(-tau * (0.5 * Jxy - 0.25 * Jz)), ea = exp(-tau * (-0.5 * Jxy - 0.25 * Jz));
+  const double u = 0.5 * (es + ea), v = 0.5 * (es - ea);
+  double g[4][4] = {{p, 0, 0, 0}, {0, u, v, 0}, {0, v, u, 0}, {0, 0, 0, p}};
+  // g = a I(x)I + b (X(x)X + Y(x)Y) + d Z(x)Z with Y(x)Y = -E(x)E, E = [[0,1],[-1,0]]:
+  // diagonal a + d = p, a - d = u; off-diagonal 2 b = v
+  const double coef[4] = {0.5 * (p + u), 0.5 * v, -0.5 * v, 0.5 * (p - u)};
+  static const double basis[4][2][2] = {
+      {{1, 0}, {0, 1}}, {{0, 1}, {1, 0}}, {{0, 1}, {-1, 0}}, {{1, 0}, {0, -1}}};
+  double A[4][2][2], B[4][2][2];
+  for (int k = 0; k < 4; ++k) {
+    const double r = sqrt(fabs(coef[k])), sg = coef[k] < 0.0 ? -r : r;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        A[k][i][j] = r * basis[k][i][j];
+        B[k][i][j] = sg * basis[k][i][j];
+      }
+  }
+  // T[x][x'][(e0 o0)][(e2 o2)] = sum_{e1,o1} g[(e1 o1)][(e0 o0)] B_x[e2][e1] A_x'[o2][o1]
+  for (int x = 0; x < 4; ++x)
+    for (int xp = 0; xp < 4; ++xp)
+      for (int y = 0; y < 4; ++y)
+        for (int yp = 0; yp < 4; ++yp) {
+          const int e0 = y >> 1, o0 = y & 1, e2 = yp >> 1, o2 = yp & 1;
+          double acc = 0.0;
+          for (int e1 = 0; e1 < 2; ++e1)
+            for (int o1 = 0; o1 < 2; ++o1)
+              acc += g[2 * e1 + o1][2 * e0 + o0] * B[x][e2][e1] * A[xp][o2][o1];
+          T0_out[((x * 4 + xp) * 4 + y) * 4 + yp] = acc;
+        }
+  return HOTRG_OK;
+}
+
 void hotrg_destroy(hotrg_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -872,6 +930,22 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
 }
 
 hotrg_status hotrg_batch_step(hotrg_ctx *c, hotrg_dir dir) { return hotrg_step(c, dir); }
+
+hotrg_status hotrg_trace_y(hotrg_ctx *c) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->status != HOTRG_OK) return c->status;
+  const double w = ldexp(1.0, -c->nsteps);
+  for (auto &gp : c->groups) {
+    Group &g = *gp;
+    CK_CUDA(c, trace_y(g.T, g.Tn, g.dx, g.dy, g.sT, g.G, c->stream));
+    CK_CUDA(c, maxabs_scale_log(g.Tn, (long long)g.dx * g.dx, g.sT, g.scal + 1, kScal, g.scal,
+                                kScal, w, g.scal + 5, kScal, c->err, g.G, c->stream));
+    std::swap(g.T, g.Tn);
+    g.dy = 1;
+  }
+  CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
 
 hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
   if (!c) return HOTRG_EINVAL;

@@ -54,6 +54,27 @@ def test_potts_tensor_matches_oracle(lib, q, beta):
                        rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("Jxy,Jz,tau", [(1.0, 1.0, 0.1), (1.0, 0.0, 1 / 32), (0.0, 1.0, 0.3),
+                                         (0.7, -0.3, 0.05), (-1.0, -1.0, 0.2), (1.0, 1.0, 2.0)])
+def test_xxz_tensor_matches_oracle(lib, Jxy, Jz, tau):
+    import paper_2602_05900_gb300 as pkg
+    from oracle import heisenberg
+    assert np.allclose(pkg.xxz_tensor(Jxy, Jz, tau), heisenberg.cell_tensor(Jxy, Jz, tau),
+                       rtol=0, atol=1e-13)
+
+
+def test_xxz_argument_validation(lib):
+    from paper_2602_05900_gb300.capi import HOTRG_EINVAL
+    buf = np.zeros(256)
+    dp = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.hotrg_xxz_tensor(1.0, 1.0, 0.0, dp) == HOTRG_EINVAL
+    assert lib.hotrg_xxz_tensor(1.0, 1.0, -0.1, dp) == HOTRG_EINVAL
+    assert lib.hotrg_xxz_tensor(float("nan"), 1.0, 0.1, dp) == HOTRG_EINVAL
+    assert lib.hotrg_xxz_tensor(1.0, float("inf"), 0.1, dp) == HOTRG_EINVAL
+    assert lib.hotrg_xxz_tensor(1.0, 1.0, 0.1, None) == HOTRG_EINVAL
+    assert lib.hotrg_trace_y(None) == HOTRG_EINVAL
+
+
 def test_host_argument_validation(lib):
     import paper_2602_05900_gb300 as pkg
     from paper_2602_05900_gb300.capi import HOTRG_EINVAL

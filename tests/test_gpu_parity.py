@@ -171,3 +171,21 @@ def test_eigensolver_paths_and_residuals(pkg, D_cut, nsteps, paths):
         assert seen <= paths and 0 in seen
         compare_steps(h, r, 1e-11)
         assert abs(h.ln_z_per_site() / r.ln_z_per_site - 1) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_graph_replay_matches_eager(pkg, prec):
+    """Contraction segments replayed from CUDA graphs (a non-NULL stream is
+    needed for capture) give bit-identical results to eager launches."""
+    torch = pytest.importorskip("torch")
+    from paper_2602_05900_gb300.capi import OPT_GRAPHS
+    stream = torch.cuda.Stream()
+    T0 = pkg.ising_tensor(0.44, 0.01)
+    out = {}
+    for graphs in (1, 0):
+        with pkg.Hotrg(T0, 16, prec, stream) as h:
+            h.set_option(OPT_GRAPHS, graphs)
+            h.run(16)
+            out[graphs] = (h.ln_z_per_site(), h.tensor())
+    assert out[1][0] == out[0][0]
+    assert np.array_equal(out[1][1], out[0][1])
