@@ -36,7 +36,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import CONFIGS, sweep256  # noqa: E402
+from workloads import CONFIGS, QUANTUM_CONFIGS, sweep256  # noqa: E402
 
 METRIC = "HOTRG RG-steps/s at steady-state D=D_cut (TF32 tensor-core contractions, FP64 eig)"
 SWEEP_METRIC = "HOTRG aggregate RG-steps/s, batched beta sweep (instance-steps/s, TF32 contractions, FP64 eig)"
@@ -44,7 +44,9 @@ EIG_NOTE = ("fp64 batched subspace iteration + two-sided Jacobi Rayleigh-Ritz (t
             "both sides), cuSOLVER syevdx fallback")
 L2_FLUSH_BYTES = 512 << 20
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor throughput
-BF16_SPLIT_PRODUCTS = {"bf16x3": 3, "bf16x6": 6}
+# BF16 tensor-core products per algorithmic product: split planes, or for the
+# exact-slice mode the 21 digit pairs (s + t <= 7) of six base-64 digits
+BF16_SPLIT_PRODUCTS = {"bf16x3": 3, "bf16x6": 6, "bf16xs": 21}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -266,7 +268,8 @@ def run_ours(args, world, rank, local):
     out = {"metric": METRIC, "value": round(value, 4), "unit": "RG-steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6", "fp64": "f64"}[prec],
+           "dtype": {"tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6", "fp64": "f64",
+                     "bf16xs": "bf16 (exact slices, FP64-grade)"}[prec],
            "data": "synthetic (analytic Ising/Potts initial tensor; no dataset)",
            "config": {"workload": cfg.name, "family": cfg.family, "beta": cfg.beta, "h": cfg.h,
                       "q": cfg.q, "D_cut": D, "steady_state_D": D, "precision": prec,
@@ -302,6 +305,7 @@ def run_ours(args, world, rank, local):
         out["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
         out["cpu_baseline_1_thread"] = cpu_baseline_single_thread(cfg)
         out["precision_modes"] = precision_modes(pkg, stream, torch)
+        out["quantum_chain"] = quantum_report(pkg, stream, torch, flush)
     return out
 
 
@@ -556,6 +560,18 @@ def run_reference(args, world, rank):
                 "config": {"workload": "sweep256", "precision": "fp64 (CPU oracle)"},
                 "cpu_baseline": vals[-1],
                 "e2e": {"value": v, "unit": "RG-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.workload in QUANTUM_CONFIGS:
+        q = QUANTUM_CONFIGS[args.workload]
+        quantum_cpu_baseline(q, budget_s=0.0, max_steps=1)             # warm-up (untimed)
+        timed = quantum_cpu_baseline(q, budget_s=60.0, max_steps=args.steps)
+        v = timed["value"]
+        return {"metric": QUANTUM_METRIC, "value": v, "unit": "update steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / v, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "impl": "reference", "data": "synthetic (analytic Trotterised cell tensor; no dataset)",
+                "config": {"workload": q.name, "D_cut": q.D_cut, "precision": "fp64 (CPU oracle)"},
+                "cpu_baseline": timed,
+                "e2e": {"value": v, "unit": "update steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     cfg = CONFIGS[args.workload]
     # each step: one steady-state oracle step (a bounded sample of the workload);
     # the timed part stops after about a minute of CPU work
@@ -573,6 +589,173 @@ def run_reference(args, world, rank):
             "e2e": {"value": v, "unit": "RG-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------- quantum chain
+
+QUANTUM_METRIC = ("quantum HOTRG update steps/s, AF Heisenberg chain (imaginary-time Y steps at "
+                  "Dx = D_cut; exact-slice FP64-grade contractions, FP64 eig)")
+# time-per-step fit exponents x (t ~ D_b^x) of the paper's HOTRG runs on the same
+# chain (Fig. 4b): context for the exponent measured here, not a target
+PAPER_HOTRG_EXPONENTS = {"fpga_piped": 2.10, "fpga_unpiped": 2.08, "gpu": 2.89, "cpu": 6.04}
+
+
+def quantum_job(pkg, q, prec, stream, torch, flush, profile=False):
+    """One whole schedule of chain q: n_time Y steps, the time trace, n_space X
+    steps.  Returns (CUDA-event ms of the Y steps taken at Dx = D_cut, each after
+    an L2 flush outside the events; ln Z / N_cells; stage profile of those steps)."""
+    times, prof = [], None
+    with pkg.Hotrg(pkg.xxz_tensor(q.Jxy, q.Jz, q.tau), q.D_cut, prec, stream) as h:
+        for _ in range(q.n_time):
+            steady = h.dims()[0] == q.D_cut
+            if steady and profile:
+                h.profile_enable(True)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.step("y")
+            b.record(stream)
+            b.synchronize()
+            if steady:
+                times.append(a.elapsed_time(b))
+        if profile:
+            prof = h.profile_read()
+            h.profile_enable(False)
+        h.trace_y()
+        for _ in range(q.n_space):
+            h.step("x")
+        lz = h.ln_z_per_site()
+    return times, lz, prof
+
+
+def fit_exponent(ds, ts):
+    """Least-squares slope of log t against log D."""
+    xs, ys = [math.log(d) for d in ds], [math.log(t) for t in ts]
+    mx, my = statistics.mean(xs), statistics.mean(ys)
+    return sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+
+
+def quantum_report(pkg, stream, torch, flush, jobs=4, precs=("bf16xs", "fp64")):
+    """Time per imaginary-time update step of the Heisenberg chain against the
+    bond dimension, its fit exponent, and each job's free energy against the
+    stored FP64 oracle value."""
+    res = {"workload": "AF Heisenberg chain, Jxy = Jz = 1, tau = 1/32, 7 Y steps (beta = 4), "
+                       "time trace, 16 X steps", "per_D": {}}
+    for name, q in QUANTUM_CONFIGS.items():
+        row = {}
+        for prec in precs:
+            quantum_job(pkg, q, prec, stream, torch, flush)            # warm-up (autotune, graphs)
+            ts, lz = [], None
+            for _ in range(jobs):
+                t, lz, _ = quantum_job(pkg, q, prec, stream, torch, flush)
+                ts += t
+            g = golden(name)
+            row[prec] = {"ms_per_update_step": round(statistics.mean(ts), 4), "updates_timed": len(ts),
+                         "free_energy": -lz / (2 * q.tau),
+                         "rel_err_vs_fp64_oracle": abs(lz / g["ln_z_per_site"] - 1) if g else None}
+        res["per_D"][q.D_cut] = row
+    ds = sorted(res["per_D"])
+    res["fit_exponent"] = {p: round(fit_exponent(ds, [res["per_D"][d][p]["ms_per_update_step"] for d in ds]), 3)
+                           for p in precs}
+    res["paper_fit_exponents_context"] = PAPER_HOTRG_EXPONENTS
+    return res
+
+
+def quantum_cpu_baseline(q, budget_s=20.0, max_steps=64):
+    """The FP64 oracle (as it stands) on the host cores: imaginary-time Y steps
+    of chain q at Dx = D_cut, timed until about budget_s of CPU work."""
+    from oracle import heisenberg, hotrg as ref
+    T = heisenberg.cell_tensor(q.Jxy, q.Jz, q.tau)
+    T = T / abs(T).max()
+    while T.shape[0] < q.D_cut:                       # transient steps (untimed)
+        T = ref.y_step(T, q.D_cut)[0]
+    n, t0 = 0, time.perf_counter()
+    while n < max(1, max_steps):
+        T = ref.y_step(T, q.D_cut)[0]
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 4), "unit": "update steps/s", "cores": os.cpu_count(),
+            "blas": blas_name(), "blas_threads": blas_threads(), "kind": "oracle",
+            "sample": f"{n} oracle Y steps of {q.name} at Dx = {q.D_cut}, Dy = 4 after the transient"}
+
+
+def run_quantum_line(args, world, rank, local):
+    import torch
+    import paper_2602_05900_gb300 as pkg
+    pkg.load()   # fails loudly if the CUDA library was not built
+    torch.cuda.set_device(local)
+    q = QUANTUM_CONFIGS[args.workload]
+    prec = args.precision or q.precision
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    warm = 0
+    while warm < args.warmup:                          # whole jobs: autotuner, graphs
+        warm += len(quantum_job(pkg, q, prec, stream, torch, flush)[0])
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    times, lz, profs = [], None, []
+    with ClockSampler(local) as clk:
+        while len(times) < args.steps:
+            t, lz, pr = quantum_job(pkg, q, prec, stream, torch, flush, profile=True)
+            times += t
+            profs.append(pr)
+    torch.cuda.synchronize()
+    barrier(world)
+    times = times[:args.steps]
+    max_ms = reduce_max(sum(times), world)
+    value = world * args.steps / (max_ms / 1e3)
+    ms = {k: sum(p["ms"][k] for p in profs) for k in profs[0]["ms"]}
+    fl = {k: sum(p["flops"][k] for p in profs) for k in profs[0]["flops"]}
+    nst = sum(p["steps"] for p in profs)
+    top = max((k for k in ms if fl[k] > 0), key=lambda k: ms[k])
+    bf16_burst, _, _, peak_src = peaks()
+    if prec == "tf32":
+        peak, note = bf16_burst * TF32_PER_BF16, f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"
+    elif prec in BF16_SPLIT_PRODUCTS:
+        peak, note = bf16_burst / BF16_SPLIT_PRODUCTS[prec], f"{peak_src} bf16 burst / products"
+    else:
+        peak, note = 1.25, "nominal FP64 (algorithmic FP64 flops)"
+    achieved = fl[top] / (ms[top] / 1e3) / 1e12 if ms[top] > 0 else 0.0
+    out = {"metric": QUANTUM_METRIC, "value": round(value, 4), "unit": "update steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"bf16xs": "bf16 (exact slices, FP64-grade)", "fp64": "f64", "tf32": "tf32",
+                     "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[prec],
+           "data": "synthetic (analytic Trotterised cell tensor of the chain; no dataset)",
+           "config": {"workload": q.name, "Jxy": q.Jxy, "Jz": q.Jz, "tau": q.tau, "beta": q.beta,
+                      "D_cut": q.D_cut, "Dy": 4, "precision": prec,
+                      "l2": f"flushed before every update step ({L2_FLUSH_BYTES >> 20} MiB write)",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": {"kernel": f"stage {top} (largest share of the update step)",
+                        "bound": "tensor" if prec != "fp64" else "alu", "achieved": round(achieved, 3),
+                        "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 5),
+                        "traffic": None, "peak_source": note},
+           "stage_ms_per_step": {k: round(v / max(1, nst), 4) for k, v in ms.items()},
+           "gpu_launches": int(sum(p["launches"] for p in profs) * args.steps / max(1, nst)),
+           "clocks": clk.summary()}
+    if rank == 0 and not args.quick:
+        g = golden(q.name)
+        out["ln_z_per_cell"] = lz
+        out["free_energy"] = -lz / (2 * q.tau)
+        out["rel_err_vs_fp64_oracle"] = abs(lz / g["ln_z_per_site"] - 1) if g else None
+        t0 = time.perf_counter()
+        for _ in range(2):
+            with pkg.Hotrg(pkg.xxz_tensor(q.Jxy, q.Jz, q.tau), q.D_cut, prec) as h:
+                h.run_quantum(q.n_time, q.n_space)
+                h.free_energy(2 * q.tau)
+        job_s = (time.perf_counter() - t0) / 2
+        out["e2e"] = {"value": round(q.n_time / job_s, 4), "unit": "update steps/s",
+                      "h2d_bytes_per_step": round(256 * 8 / q.n_time, 2),
+                      "d2h_bytes_per_step": round(8 * 8 / q.n_time, 2),
+                      "note": "whole schedule through the public API from host memory (cell tensor "
+                              "H2D at create, ln Z D2H), per Y update"}
+        out["cpu_baseline"] = quantum_cpu_baseline(q, budget_s=args.cpu_budget)
+    return out
+
+
 # ----------------------------------------------------------------------------- main
 
 def main():
@@ -580,7 +763,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=120)   # ~1 s timed at D=32: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="ising_044_d32", choices=sorted(CONFIGS) + ["sweep256"])
+    ap.add_argument("--workload", default="ising_044_d32",
+                    choices=sorted(CONFIGS) + ["sweep256"] + sorted(QUANTUM_CONFIGS))
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6", "bf16xs"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU legs")
@@ -604,6 +788,8 @@ def main():
         out = run_reference(args, world, rank)
     elif args.workload == "sweep256":
         out = run_sweep(args, world, rank, local)
+    elif args.workload in QUANTUM_CONFIGS:
+        out = run_quantum_line(args, world, rank, local)
     else:
         out = run_ours(args, world, rank, local)
     if rank == 0 and out is not None:

@@ -1,9 +1,11 @@
 """Write ``oracle_values.json``: FP64 oracle results for the benchmark workloads.
 
 Calls only ``oracle/`` and the workload parameters in ``workloads/``; the CUDA
-library is never imported.  Each entry holds ln Z / N after the workload's
-step count, the free energy per site, and the per-step ln c_n, discarded
-weights, side and normalised spectrum head of the chosen environment.
+library is never imported.  Each classical entry holds ln Z / N after the
+workload's step count, the free energy per site, and the per-step ln c_n,
+discarded weights, side and normalised spectrum head of the chosen
+environment; each quantum-chain entry (D_cut <= 32) holds ln Z / N_cells and
+the free energy per site of the whole schedule.
 
     python tests/golden/make_oracle_values.py [name ...]
 
@@ -17,8 +19,8 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-from oracle import hotrg  # noqa: E402
-from workloads import CONFIGS  # noqa: E402
+from oracle import heisenberg, hotrg  # noqa: E402
+from workloads import CONFIGS, QUANTUM_CONFIGS  # noqa: E402
 
 OUT = os.path.join(HERE, "oracle_values.json")
 
@@ -46,12 +48,26 @@ def compute(cfg):
     }
 
 
+def compute_quantum(q):
+    t0 = time.time()
+    r = heisenberg.run(heisenberg.cell_tensor(q.Jxy, q.Jz, q.tau), q.D_cut, q.n_time, q.n_space)
+    lz = r.ln_z_per_site
+    return {
+        "family": "xxz_chain", "Jxy": q.Jxy, "Jz": q.Jz, "tau": q.tau, "beta": q.beta,
+        "n_time": q.n_time, "n_space": q.n_space, "D_cut": q.D_cut,
+        "ln_z_per_site": lz, "free_energy": heisenberg.free_energy_per_site(lz, q.tau),
+        "min_cut_gap": min([s.cut_gap for s in r.steps if s.Dn < s.Dx * s.Dx] or [None]),
+        "oracle_seconds": time.time() - t0,
+    }
+
+
 def main(names):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
-    todo = names or [n for n in CONFIGS if n not in data]
+    every = list(CONFIGS) + [n for n in QUANTUM_CONFIGS if QUANTUM_CONFIGS[n].D_cut <= 32]
+    todo = names or [n for n in every if n not in data]
     for name in todo:
         print(f"oracle: {name} ...", flush=True)
-        data[name] = compute(CONFIGS[name])
+        data[name] = compute(CONFIGS[name]) if name in CONFIGS else compute_quantum(QUANTUM_CONFIGS[name])
         print(f"  ln Z/N = {data[name]['ln_z_per_site']:.16f} ({data[name]['oracle_seconds']:.0f} s)", flush=True)
         json.dump(data, open(OUT, "w"), indent=1)
 

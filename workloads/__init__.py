@@ -16,6 +16,10 @@ The five model configurations are the ones the benchmarks are quoted on:
 
 All directions alternate starting with X.  Random draws use
 ``numpy.random.default_rng(SEED)``.
+
+Quantum chains (``QUANTUM_CONFIGS``): the antiferromagnetic Heisenberg chain,
+tau = 1/32, 7 imaginary-time steps (beta = 4), 16 chain steps, D_cut in
+{8, 16, 32, 64}, exact-slice (FP64-grade) contractions.
 """
 from __future__ import annotations
 
@@ -48,6 +52,33 @@ CONFIGS = {
     "ising_044_d32": Model("ising_044_d32", "ising", 0.44, 0.0, 2, 32, 30, "tf32"),
     "ising_044h_d48": Model("ising_044h_d48", "ising", 0.44, 0.01, 2, 48, 30, "bf16x3"),
     "potts3_d64": Model("potts3_d64", "potts", BETA_C_POTTS3, 0.0, 3, 64, 30, "bf16x3"),
+}
+
+
+@dataclass(frozen=True)
+class QuantumChain:
+    """Finite-temperature quantum HOTRG of the spin-1/2 XXZ chain: the
+    Trotterised two-site cell tensor with step tau, n_time Y steps along
+    imaginary time (beta = 2^n_time tau), the time trace, n_space X steps."""
+    name: str
+    Jxy: float
+    Jz: float
+    tau: float
+    n_time: int
+    n_space: int
+    D_cut: int
+    precision: str = "bf16xs"
+
+    @property
+    def beta(self) -> float:
+        return self.tau * 2 ** self.n_time
+
+
+# The antiferromagnetic Heisenberg chain (Jxy = Jz = 1) at beta = 4 with
+# tau = 1/32; the update-step timings sweep the bond dimension D_cut.
+QUANTUM_CONFIGS = {
+    f"heisenberg_b4_d{D}": QuantumChain(f"heisenberg_b4_d{D}", 1.0, 1.0, 1 / 32, 7, 16, D, "bf16xs")
+    for D in (8, 16, 32, 64)
 }
 
 
