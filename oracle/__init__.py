@@ -19,6 +19,8 @@ Contents
 ``heisenberg``  quantum HOTRG of the spin-1/2 XXZ chain: the Trotterised
                 imaginary-time cell tensor (Sec. II.A-B), dense small-chain
                 references, and the schedule Y steps -> time trace -> X steps.
+``itebd``       iTEBD ground state of the XXZ chain (Sec. II.A, Eq. 1): two-site
+                gate updates with SVD truncation, bond and site energies.
 ``sampled``     element-by-element evaluation of single-step outputs, for checks
                 at sizes where the full oracle is too slow.
 

@@ -99,6 +99,16 @@ def random_tensor(D0: int, seed: int = SEED, Dy: int | None = None) -> np.ndarra
     return rng.random((D0, D0, Dy, Dy))
 
 
+def random_mps(D: int, d: int = 2, seed: int = SEED):
+    """Seeded random two-site-cell MPS state (P, Q, lam): P, Q i.i.d. N(0, 1) of
+    shape (D, d, D), lam positive, descending, with sum lam^2 = 1."""
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal((D, d, D))
+    Q = rng.standard_normal((D, d, D))
+    lam = np.sort(rng.uniform(0.1, 1.0, size=D))[::-1]
+    return P, Q, lam / np.linalg.norm(lam)
+
+
 def random_orthogonal(n: int, seed: int = SEED) -> np.ndarray:
     """Haar-random orthogonal matrix (QR of a Gaussian matrix, sign-fixed)."""
     rng = np.random.default_rng(seed)
