@@ -306,6 +306,8 @@ def run_ours(args, world, rank, local):
         out["cpu_baseline_1_thread"] = cpu_baseline_single_thread(cfg)
         out["precision_modes"] = precision_modes(pkg, stream, torch)
         out["quantum_chain"] = quantum_report(pkg, stream, torch, flush)
+        out["itebd"] = itebd_report(pkg, torch)
+        out["itebd"]["cpu_baseline"] = itebd_cpu_baseline()
     return out
 
 
@@ -659,6 +661,61 @@ def quantum_report(pkg, stream, torch, flush, jobs=4, precs=("bf16xs", "fp64")):
                            for p in precs}
     res["paper_fit_exponents_context"] = PAPER_HOTRG_EXPONENTS
     return res
+
+
+# iTEBD time-per-update fit exponents of the paper's runs on the same chain
+# (Fig. 4a, D_b <= 30 on CPU / GPU): context, not a target
+PAPER_ITEBD_EXPONENTS = {"fpga_piped": 1.11, "fpga_unpiped": 1.09, "gpu": 1.14, "cpu": 2.94}
+
+
+def itebd_report(pkg, torch, d_values=(4, 8, 12, 16, 20, 24, 30, 48), batch=64, warm=60, n=200):
+    """iTEBD of the AF Heisenberg chain (tau = 0.05, Neel start): wall time per
+    update (host timer around hotrg_itebd_step, which synchronises once) for
+    one chain and for a batch of chains, against D_b; the fit exponent; and the
+    energy per site against the Bethe-ansatz value."""
+    e0 = 0.25 - math.log(2.0)      # Bethe-ansatz ground-state energy per site (J = 1)
+    res = {"workload": f"AF Heisenberg chain, tau = 0.05, Neel start, {warm} + {n} updates; "
+                       f"FP64 (GEMMs, cluster Jacobi eig of the 2D_b x 2D_b bond density matrix)",
+           "per_D": {}}
+    for D in d_values:
+        row = {}
+        for G in (1, batch):
+            with pkg.Itebd([(1.0, 1.0, 0.05)] * G, D) as c:
+                c.step(warm)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c.step(n)
+                dt = time.perf_counter() - t0
+                e = float(c.energy()[0])
+            row[f"chains_{G}"] = {"ms_per_update": round(dt / n * 1e3, 4),
+                                  "chain_updates_per_s": round(G * n / dt, 1)}
+        row["energy_minus_bethe"] = e - e0
+        res["per_D"][D] = row
+    ds = [d for d in d_values if d <= 30]
+    res["fit_exponent_single_chain_Db_le_30"] = round(
+        fit_exponent(ds, [res["per_D"][d]["chains_1"]["ms_per_update"] for d in ds]), 3)
+    res["paper_fit_exponents_context"] = PAPER_ITEBD_EXPONENTS
+    return res
+
+
+def itebd_cpu_baseline(d_values=(8, 16, 30), budget_s=4.0, warm=60):
+    """The FP64 oracle's iTEBD update (as it stands) on the host cores, per D_b:
+    updates per second after a warm-up that grows the bond to D_b."""
+    from oracle import heisenberg, itebd
+    g = heisenberg.bond_gate(1.0, 1.0, 0.05)
+    out = {}
+    for D in d_values:
+        st = itebd.run(1.0, 1.0, 0.05, D, warm)
+        P, Q, lam = st.P, st.Q, st.lam
+        k, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            P, Q, lam, _ = itebd.update(P, Q, lam, g, D)
+            k += 1
+        out[D] = round(k / (time.perf_counter() - t0), 2)
+    return {"value_updates_per_s": out, "unit": "update steps/s", "cores": os.cpu_count(),
+            "blas": blas_name(), "blas_threads": blas_threads(), "kind": "oracle",
+            "sample": f"oracle iTEBD updates of the Heisenberg chain, ~{budget_s:.0f} s per D_b after "
+                      f"{warm} warm-up updates"}
 
 
 def quantum_cpu_baseline(q, budget_s=20.0, max_steps=64):

@@ -164,6 +164,54 @@ hotrg_status hotrg_xxz_tensor(double Jxy, double Jz, double tau, double *T0_out)
 hotrg_status hotrg_trace_y(hotrg_ctx *ctx);
 
 /*
+ * iTEBD ground states of the XXZ chain (Sec. II.A, Eq. 1: the two-site-cell
+ * matrix-product state ... lambda_2 A lambda_1 B lambda_2 ..., driven to the
+ * ground state by imaginary-time gates U = exp(-tau h); the truncation is an SVD
+ * taken, as in Sec. II.B, from the two-sided Jacobi eigendecomposition of a
+ * Hermitian matrix: here the bond's reduced density matrix theta^T theta).
+ *
+ * A context holds n independent chains with the same bond cap D_b; chain i has
+ * couplings[3i .. 3i+2] = (Jxy, Jz, tau), h as for hotrg_xxz_tensor.  The state
+ * of a chain is (P, Q, lam): P[i][a][j] (outer x 2 x mid) and Q[j][b][m]
+ * (mid x 2 x outer), row-major FP64, in right-canonical form (Gamma lambda), and
+ * lam the Schmidt values on P's left bond (outer of them); a = 0 is Sz = +1/2.
+ * One update applies U to the (P, Q) bond:
+ *   phit = U (P Q), theta = lam[i] phit as a (2 outer) x (2 outer) matrix,
+ *   Y, w = leading D' = min(D_b, 2 outer) eigenpairs of theta^T theta,
+ *   lam' = sqrt(w) / |sqrt(w)|, P' = phit Y, Q' = Y^T,
+ * and continues with (P, Q, lam) <- (Q', P', lam') on the other kind of bond.
+ *
+ * hotrg_itebd_create: 1 <= n <= 65535, 1 <= D_b <= 48, tau > 0, finite
+ *   couplings.  P0s / Q0s / lam0s: per chain, host arrays of D0*2*D0, D0*2*D0
+ *   and D0 doubles (borrowed, copied), or all NULL for the Neel state
+ *   (P = |up>, Q = |down>, D0 must be 1).  The other bond's Schmidt values start
+ *   uniform, 1/sqrt(D0).  stream: a cudaStream_t (NULL = legacy default).  All
+ *   device memory is allocated here (HOTRG_ENOMEM if it does not fit).
+ * hotrg_itebd_step: nsteps updates of every chain; synchronises once at the
+ *   end; HOTRG_ENONFINITE if a bond's density matrix lost all positive weight.
+ * hotrg_itebd_energy: energy per site of every chain into out_n[n]: the mean
+ *   of <theta|h|theta>/<theta|theta> over the two bonds, theta = lam (P Q) and
+ *   lam_other (Q P) (the Schmidt values of each bond's left neighbour).
+ * hotrg_itebd_lambda: the current lam of chain inst (cap >= outer); *n = outer.
+ * hotrg_itebd_discarded: discarded weight sum_{k >= D'} w_k / sum_k w_k of
+ *   chain inst's last update (0 before the first).
+ * hotrg_itebd_dims: outer and mid bond dimensions and the updates taken.
+ * Errors are sticky per context, as for hotrg_ctx.
+ */
+typedef struct hotrg_itebd hotrg_itebd;
+
+hotrg_status hotrg_itebd_create(int n, const double *couplings, int D_b, int D0,
+                                const double *const *P0s, const double *const *Q0s,
+                                const double *const *lam0s, void *stream, hotrg_itebd **out);
+hotrg_status hotrg_itebd_step(hotrg_itebd *ctx, int nsteps);
+hotrg_status hotrg_itebd_energy(hotrg_itebd *ctx, double *out_n);
+hotrg_status hotrg_itebd_lambda(hotrg_itebd *ctx, int inst, double *buf, int cap, int *n);
+hotrg_status hotrg_itebd_discarded(hotrg_itebd *ctx, int inst, double *out);
+hotrg_status hotrg_itebd_dims(hotrg_itebd *ctx, int *outer, int *mid, long long *nsteps);
+const char *hotrg_itebd_last_error(const hotrg_itebd *ctx);
+void hotrg_itebd_destroy(hotrg_itebd *ctx);
+
+/*
  * Create a context holding T0 (host, D0^4 doubles, [x,x',y,y'] row-major,
  * borrowed and copied) scaled by its max-norm, ready for steps with cut D_cut.
  * stream: a cudaStream_t (NULL = the legacy default stream); the context

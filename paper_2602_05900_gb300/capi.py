@@ -65,6 +65,18 @@ _SIGS = {
     "hotrg_potts_tensor": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _dp]),
     "hotrg_xxz_tensor": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]),
     "hotrg_trace_y": (ctypes.c_int, [ctypes.c_void_p]),
+    "hotrg_itebd_create": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "hotrg_itebd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hotrg_itebd_energy": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "hotrg_itebd_lambda": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "hotrg_itebd_discarded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "hotrg_itebd_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+    "hotrg_itebd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hotrg_itebd_destroy": (None, [ctypes.c_void_p]),
     "hotrg_create": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "hotrg_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -345,6 +357,79 @@ class HotrgBatch:
         self._check(load().hotrg_batch_get_tensor(self._h, inst, _ptr(out), out.size, dims),
                     "hotrg_batch_get_tensor")
         return out
+
+
+class Itebd:
+    """A batch of iTEBD chains on the GPU (``hotrg_itebd_*``).
+
+    ``couplings`` is a sequence of (Jxy, Jz, tau), one per chain; ``init`` is
+    None (the Neel state) or one (P, Q, lam) per chain, all with the same D0.
+    """
+
+    def __init__(self, couplings, D_b: int, init=None, stream=None):
+        lib = load()
+        cp = np.ascontiguousarray(np.asarray(couplings, dtype=np.float64).reshape(-1, 3))
+        n = cp.shape[0]
+        self._keep = [cp]
+        arrays = [None, None, None]
+        D0 = 1
+        if init is not None:
+            if len(init) != n:
+                raise ValueError("need one initial state per chain")
+            D0 = int(np.asarray(init[0][2]).size)
+            for k in range(3):
+                parts = [np.ascontiguousarray(st[k], dtype=np.float64) for st in init]
+                self._keep += parts
+                arrays[k] = ctypes.cast((_dp * n)(*[_ptr(a) for a in parts]), ctypes.c_void_p)
+        handle = ctypes.c_void_p()
+        s = lib.hotrg_itebd_create(n, _ptr(cp), int(D_b), D0, arrays[0], arrays[1], arrays[2],
+                                   _stream_handle(stream), ctypes.byref(handle))
+        if s:
+            raise HotrgError(s, f"hotrg_itebd_create failed: {status_string(s)}")
+        self._h = handle
+        self.n = n
+        self.D_b = int(D_b)
+
+    def _check(self, s: int, what: str):
+        if s:
+            msg = load().hotrg_itebd_last_error(self._h)
+            raise HotrgError(s, f"{what}: {status_string(s)}: {msg.decode() if msg else ''}")
+
+    def step(self, nsteps: int = 1):
+        self._check(load().hotrg_itebd_step(self._h, int(nsteps)), "hotrg_itebd_step")
+        return self
+
+    def energy(self) -> np.ndarray:
+        out = np.zeros(self.n)
+        self._check(load().hotrg_itebd_energy(self._h, _ptr(out)), "hotrg_itebd_energy")
+        return out
+
+    def lam(self, inst: int = 0) -> np.ndarray:
+        buf = np.zeros(self.D_b)
+        k = ctypes.c_int()
+        self._check(load().hotrg_itebd_lambda(self._h, inst, _ptr(buf), buf.size, ctypes.byref(k)),
+                    "hotrg_itebd_lambda")
+        return buf[:k.value].copy()
+
+    def discarded(self, inst: int = 0) -> float:
+        out = ctypes.c_double()
+        self._check(load().hotrg_itebd_discarded(self._h, inst, ctypes.byref(out)), "hotrg_itebd_discarded")
+        return out.value
+
+    def dims(self):
+        o, m, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        self._check(load().hotrg_itebd_dims(self._h, ctypes.byref(o), ctypes.byref(m), ctypes.byref(k)),
+                    "hotrg_itebd_dims")
+        return o.value, m.value, k.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().hotrg_itebd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = Hotrg.__del__
+    __enter__ = Hotrg.__enter__
+    __exit__ = Hotrg.__exit__
 
 
 def dgemm_emu(A, B, C, slices: int = 7, stream=None):

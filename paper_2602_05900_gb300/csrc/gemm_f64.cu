@@ -5,6 +5,7 @@
 // for B and C (see IdxMap).  64 x 64 output tile per 256-thread block, 4 x 4
 // outputs per thread, K staged through shared memory in chunks of 16 with a
 // register prefetch of the next chunk; grid.z runs over the instances of a batch.
+// GEMMs with at most 64 outputs and K >= 256 take a block-per-output dot kernel.
 #include "common.cuh"
 
 namespace hotrg {
@@ -125,10 +126,40 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(MappedGemm g) {
   }
 }
 
+// Few outputs over a long K (e.g. the 1 x 1 environment of a step whose fused
+// legs are trivial, K = E^2): one block per output element, K strided over the
+// threads and combined by a fixed-order tree, so the result is deterministic.
+__global__ void __launch_bounds__(NT) k_dot_f64(MappedGemm g) {
+  __shared__ double red[NT];
+  const long long e = blockIdx.x;
+  const long long m = e / g.N, n = e % g.N;
+  g.A += blockIdx.z * g.bA;
+  g.B += blockIdx.z * g.bB;
+  g.C += blockIdx.z * g.bC;
+  const long long ao = map_off(g.am, m), bo = map_off(g.bn, n);
+  double v = 0.0;
+  for (int k = threadIdx.x; k < g.K; k += NT)
+    v = fma(g.A[ao + map_off(g.ak, k)], g.B[bo + map_off(g.bk, k)], v);
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) g.C[map_off(g.cm, m) + map_off(g.cn, n)] = red[0];
+}
+
+constexpr long long kDotMaxOutputs = 64, kDotMinK = 256;
+
 }  // namespace
 
 cudaError_t gemm_f64(const MappedGemm &g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if ((long long)g.M * g.N <= kDotMaxOutputs && g.K >= kDotMinK) {
+    if (g.batch > 65535) return cudaErrorInvalidConfiguration;
+    k_dot_f64<<<dim3((unsigned)(g.M * g.N), 1, (unsigned)(g.batch < 1 ? 1 : g.batch)), NT, 0, s>>>(g);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
             (unsigned)(g.batch < 1 ? 1 : g.batch));
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;

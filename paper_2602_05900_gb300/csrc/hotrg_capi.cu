@@ -39,6 +39,7 @@
 #include "tc_exact.cuh"
 #include "tc_gemm.cuh"
 #include "tc_path.cuh"
+#include "xxz.cuh"
 
 using namespace hotrg;
 
@@ -861,11 +862,9 @@ hotrg_status hotrg_potts_tensor(int q, double beta, double *T0_out) {
 hotrg_status hotrg_xxz_tensor(double Jxy, double Jz, double tau, double *T0_out) {
   if (!T0_out || !(tau > 0.0) || !isfinite(tau) || !isfinite(Jxy) || !isfinite(Jz))
     return HOTRG_EINVAL;
-  // gate g = exp(-tau h) from the spectrum of h: |uu>, |dd> -> Jz/4,
-  // (|ud> + |du>)/sqrt2 -> Jxy/2 - Jz/4, (|ud> - |du>)/sqrt2 -> -Jxy/2 - Jz/4
-  const double p = exp(-0.25 * tau * Jz);
-  const double es = exp(-tau * (0.5 * Jxy - 0.25 * Jz)), ea = exp(-tau * (-0.5 * Jxy - 0.25 * Jz));
-  const double u = 0.5 * (es + ea), v = 0.5 * (es - ea);
+  double gf[16];
+  xxz_gate(Jxy, Jz, tau, gf);
+  const double p = gf[0], u = gf[5], v = gf[6];
   double g[4][4] = {{p, 0, 0, 0}, {0, u, v, 0}, {0, v, u, 0}, {0, 0, 0, p}};
   // g = a I(x)I + b (X(x)X + Y(x)Y) + d Z(x)Z with Y(x)Y = -E(x)E, E = [[0,1],[-1,0]]:
   // diagonal a + d = p, a - d = u; off-diagonal 2 b = v

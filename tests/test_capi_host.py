@@ -75,6 +75,25 @@ def test_xxz_argument_validation(lib):
     assert lib.hotrg_trace_y(None) == HOTRG_EINVAL
 
 
+def test_itebd_argument_validation(lib):
+    from paper_2602_05900_gb300.capi import HOTRG_EINVAL
+    cp = np.array([1.0, 1.0, 0.05])
+    dp = cp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    bad = [(0, dp, 8, 1), (1, None, 8, 1), (1, dp, 0, 1), (1, dp, 49, 1), (1, dp, 8, 2), (1, dp, 8, 0)]
+    for n, c, Db, D0 in bad:      # rejected before any device work
+        assert lib.hotrg_itebd_create(n, c, Db, D0, None, None, None, None, ctypes.byref(h)) == HOTRG_EINVAL
+        assert h.value is None
+    for vals in ([1.0, 1.0, 0.0], [1.0, 1.0, -0.1], [float("nan"), 1.0, 0.1], [1.0, float("inf"), 0.1]):
+        cb = np.array(vals)
+        assert lib.hotrg_itebd_create(1, cb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 8, 1,
+                                      None, None, None, None, ctypes.byref(h)) == HOTRG_EINVAL
+    assert lib.hotrg_itebd_create(1, dp, 8, 1, None, None, None, None, None) == HOTRG_EINVAL
+    assert lib.hotrg_itebd_step(None, 1) == HOTRG_EINVAL
+    assert lib.hotrg_itebd_energy(None, dp) == HOTRG_EINVAL
+    lib.hotrg_itebd_destroy(None)   # NULL-safe
+
+
 def test_host_argument_validation(lib):
     import paper_2602_05900_gb300 as pkg
     from paper_2602_05900_gb300.capi import HOTRG_EINVAL
