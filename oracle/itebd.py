@@ -23,8 +23,10 @@ implementing them on its own):
   phit[i, a', b', m] = sum_{a b} g[(a' b'), (a b)] phi[i, a, b, m];
   theta = lam[i] phit, viewed as the (D_l d) x (d D_r) matrix M[(i a'), (b' m)].
 * M = X S Y^T (SVD); D' = min(D_b, rank); the new Schmidt values are
-  S[:D'] / |S[:D']|; Q' = Y[:, :D']^T viewed as [j, b', m]; P' = phit Y[:, :D']
-  viewed as [i, a', j] (= Gamma' lambda' without dividing by the old lambda).
+  S[:D'] / |S[:D']|; Q' = Y[:, :D']^T viewed as [j, b', m]; P' = phit Y[:, :D'] / |S[:D']|
+  viewed as [i, a', j] (= Gamma' lambda' without dividing by the old lambda; the
+  division by |S[:D']| keeps the state normalised, which the non-unitary
+  imaginary-time gate does not: its scale would drift by exp(-tau e) per update).
 * The next update acts on the other kind of bond: (P, Q, lam) <- (Q', P', S').
 
 Energy per bond: <theta|h|theta> / <theta|theta> with theta = lam[i] phi (the
@@ -73,8 +75,9 @@ def update(P: np.ndarray, Q: np.ndarray, lam: np.ndarray, g: np.ndarray, D_b: in
     disc = float(np.sum(w[Dn:]) / np.sum(w))
     Y = Yt[:Dn].T                                       # (d Dr, Dn)
     Qn = Yt[:Dn].reshape(Dn, d, Dr)
-    Pn = (phit.reshape(Dl * d, d * Dr) @ Y).reshape(Dl, d, Dn)
-    sn = s[:Dn] / np.linalg.norm(s[:Dn])
+    norm = np.linalg.norm(s[:Dn])
+    Pn = (phit.reshape(Dl * d, d * Dr) @ Y).reshape(Dl, d, Dn) / norm
+    sn = s[:Dn] / norm
     return Qn, Pn, sn, disc
 
 

@@ -20,13 +20,14 @@ def test_update_without_truncation_is_exact():
     phi = np.einsum("iaj,jbm->iabm", P, Q)
     phit = np.einsum("ABab,iabm->iABm", g.reshape(2, 2, 2, 2), phi).reshape(6, 6)
     assert disc == 0.0 or disc < 1e-28
-    assert np.allclose(Pn.reshape(6, -1) @ Qn.reshape(Qn.shape[0], -1), phit, rtol=0, atol=1e-13)
+    s_full = np.linalg.svd((lam[:, None, None] * phit.reshape(3, 2, 6)).reshape(6, 6), compute_uv=False)
+    norm = np.linalg.norm(s_full)                                # the state is renormalised
+    assert np.allclose(Pn.reshape(6, -1) @ Qn.reshape(Qn.shape[0], -1) * norm, phit, rtol=0, atol=1e-13)
     Qm = Qn.reshape(Qn.shape[0], -1)
     assert np.allclose(Qm @ Qm.T, np.eye(Qm.shape[0]), rtol=0, atol=1e-14)   # right-canonical
     assert abs(np.sum(sn * sn) - 1.0) < 1e-15 and np.all(np.diff(sn) <= 0)
     # the Schmidt values are the singular values of the lam-weighted gated pair
-    s_full = np.linalg.svd((lam[:, None, None] * phit.reshape(3, 2, 6)).reshape(6, 6), compute_uv=False)
-    assert np.allclose(sn, s_full / np.linalg.norm(s_full), rtol=0, atol=1e-14)
+    assert np.allclose(sn, s_full / norm, rtol=0, atol=1e-14)
 
 
 @pytest.mark.parametrize("Jxy,Jz,tau", [(1.0, 1.0, 0.1), (1.0, 0.0, 0.3), (0.7, -0.3, 0.2)])
@@ -71,6 +72,13 @@ def test_ground_energy_limits(Jxy, Jz, exact):
     assert exact < e2 < e1                          # above the ground state, falling with tau
     assert abs(ex8 - exact) < 6e-4
     assert abs(ex16 - exact) < 1e-4 and abs(ex16 - exact) < abs(ex8 - exact)
+
+
+def test_state_stays_normalised_over_long_runs():
+    # 20000 updates at tau = 0.05 would scale an unnormalised state by ~exp(750)
+    st = it.run(1.0, 1.0, 0.05, 4, 20000)
+    assert np.all(np.isfinite(st.P)) and np.all(np.isfinite(st.Q))
+    assert 1e-3 < np.linalg.norm(st.P) < 1e3
 
 
 def test_energy_falls_with_bond_dimension():
