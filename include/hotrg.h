@@ -178,7 +178,8 @@ hotrg_status hotrg_trace_y(hotrg_ctx *ctx);
  * One update applies U to the (P, Q) bond:
  *   phit = U (P Q), theta = lam[i] phit as a (2 outer) x (2 outer) matrix,
  *   Y, w = leading D' = min(D_b, 2 outer) eigenpairs of theta^T theta,
- *   lam' = sqrt(w) / |sqrt(w)|, P' = phit Y, Q' = Y^T,
+ *   lam' = sqrt(w) / |sqrt(w)|, P' = phit Y / |sqrt(w)| (the state stays
+ *   normalised under the non-unitary gate), Q' = Y^T,
  * and continues with (P, Q, lam) <- (Q', P', lam') on the other kind of bond.
  *
  * hotrg_itebd_create: 1 <= n <= 65535, 1 <= D_b <= 48, tau > 0, finite

@@ -9,7 +9,8 @@
 //                                      reduced density matrix (2D x 2D)
 //   Y, w  = eig(rho)                   cluster two-sided Jacobi (Sec. II.B, Eqs. 5-6)
 //   lam'  = sqrt(w[:D']) / norm        k_itebd_schmidt (+ the discarded weight)
-//   P'    = phit Y[:, :D']             FP64 GEMM
+//   P'    = phit Y[:, :D'] / |s|       FP64 GEMM + k_itebd_scale (keeps the state
+//                                      normalised under the non-unitary gate)
 //   Q'    = Y[:, :D']^T                k_itebd_take (Y is column-major: a copy)
 //
 // then (P, Q, lam) <- (Q', P', lam') for the other kind of bond.  The singular
@@ -63,9 +64,10 @@ __global__ void k_itebd_gate(const double *phi, double *phit, double *theta, con
 }
 
 // one block per chain: lam'[k] = sqrt(w_k) / sqrt(sum_{k < Dn} w_k) with w = max(eig, 0);
-// disc = sum_{k >= Dn} w_k / sum_k w_k over the m eigenvalues (descending)
+// disc = sum_{k >= Dn} w_k / sum_k w_k over the m eigenvalues (descending);
+// rnorm = 1 / sqrt(sum_{k < Dn} w_k), the factor that keeps the state normalised
 __global__ void k_itebd_schmidt(PSet w, int m, int Dn, double *lam, long long sL, double *disc,
-                                int *err) {
+                                double *rnorm, int *err) {
   const int z = blockIdx.x;
   const double *wz = w.at(z);
   __shared__ double keep;
@@ -78,11 +80,21 @@ __global__ void k_itebd_schmidt(PSet w, int m, int Dn, double *lam, long long sL
     }
     keep = a;
     disc[z] = b > 0.0 ? (b - a) / b : NAN;
+    rnorm[z] = 1.0 / sqrt(a);
     if (!(a > 0.0) || !isfinite(b)) atomicExch(err, 1);
   }
   __syncthreads();
   const double inv = 1.0 / sqrt(keep);
   for (int k = threadIdx.x; k < Dn; k += blockDim.x) lam[z * sL + k] = sqrt(fmax(wz[k], 0.0)) * inv;
+}
+
+// P' *= rnorm of its chain
+__global__ void k_itebd_scale(double *P, long long count, long long sT, const double *rnorm) {
+  const long long z = blockIdx.y;
+  const double r = rnorm[z];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    P[z * sT + e] *= r;
 }
 
 // Q'[j][B][m] = Y[(B m), j] for j < Dn: the first Dn columns of the column-major Y
@@ -148,6 +160,7 @@ struct hotrg_itebd {
   int iL = 0, iO = 1;
   double *phi = nullptr, *phit = nullptr, *theta = nullptr, *rho = nullptr;
   double *gates = nullptr, *hs = nullptr, *disc = nullptr, *energy = nullptr, *trace = nullptr;
+  double *rnorm = nullptr;
   double *si_work = nullptr;
   int *err = nullptr;
   std::vector<void *> allocs;
@@ -222,13 +235,16 @@ hotrg_status itebd_update(hotrg_itebd *c) {
   long long nl = 0;
   ICK(c, jacobi_full(sb, c->si_work, st, &nl));
   const SiOut o = si_outputs(c->si_work, G, n, sb.m);
-  k_itebd_schmidt<<<G, 64, 0, st>>>(o.theta, sb.m, Dn, c->l[iN], c->sL, c->disc, c->err);
+  k_itebd_schmidt<<<G, 64, 0, st>>>(o.theta, sb.m, Dn, c->l[iN], c->sL, c->disc, c->rnorm, c->err);
   ICK(c, cudaGetLastError());
   // P' = phit Y, Q' = Y^T
   const long long ys = o.X.b1 - o.X.b0;
   MappedGemm g3{kPhys * Dl, Dn, n, c->phit, map1(n), map1(1), o.X.b0, map1(n), map1(1), Pn, map1(Dn),
                 map1(1), G, c->sM, ys, c->sT};
   ICK(c, gemm_f64(g3, st));
+  k_itebd_scale<<<dim3(grid1((long long)kPhys * Dl * Dn), G), 256, 0, st>>>(Pn, (long long)kPhys * Dl * Dn,
+                                                                           c->sT, c->rnorm);
+  ICK(c, cudaGetLastError());
   k_itebd_take<<<dim3(grid1((long long)Dn * n), G), 256, 0, st>>>(o.X, (long long)Dn * n, Qn, c->sT);
   ICK(c, cudaGetLastError());
   // the next bond: (P, Q, lam) <- (Q', P', lam'); lam_other <- lam
@@ -289,7 +305,7 @@ hotrg_status hotrg_itebd_create(int n, const double *couplings, int D_b, int D0,
       (s = ialloc(c, &c->theta, c->sM * n)) || (s = ialloc(c, &c->rho, c->sM * n)) ||
       (s = ialloc(c, &c->gates, 16LL * n)) || (s = ialloc(c, &c->hs, 16LL * n)) ||
       (s = ialloc(c, &c->disc, (long long)n)) || (s = ialloc(c, &c->energy, 2LL * n)) ||
-      (s = ialloc(c, &c->trace, (long long)n)) ||
+      (s = ialloc(c, &c->trace, (long long)n)) || (s = ialloc(c, &c->rnorm, (long long)n)) ||
       (s = ialloc(c, &c->si_work, si_workspace_doubles(n, (int)twoD, jacobi_block((int)twoD)))) ||
       (s = ialloc(c, &c->err, 4LL)))
     return bail(s);

@@ -93,6 +93,16 @@ def test_fp64_xx_ground_energy_extrapolation(pkg):
     assert abs(ex - it.xx_ground_energy(1.0)) < 1e-4
 
 
+def test_fp64_long_run_stays_normalised(pkg):
+    """20000 updates at tau = 0.05 (an unnormalised state would grow by ~e^750):
+    finite, and at D_b = 4 (no degenerate cut after the transient) equal to the
+    oracle's energy."""
+    ref = it.site_energy(it.run(1.0, 1.0, 0.05, 4, 20000), hz.bond_hamiltonian(1.0, 1.0))
+    with pkg.Itebd([(1.0, 1.0, 0.05)], 4) as c:
+        e = c.step(20000).energy()[0]
+    assert np.isfinite(e) and abs(e - ref) < 1e-6
+
+
 @pytest.mark.parametrize("Jz", [1.0, 2.5])
 def test_fp64_ising_limit(pkg, Jz):
     with pkg.Itebd([(0.0, Jz, 0.1)], 4) as c:
