@@ -43,6 +43,7 @@ constexpr int kRowsPerChunk = 16;
 constexpr int kCluster = 8;      // CTAs per Jacobi problem (one thread-block cluster)
 constexpr int kJacobiMaxSweeps = 40;
 constexpr int kCholThreads = 256;
+constexpr int kCholPanel = 8;      // columns per panel of the blocked FP32 Cholesky
 constexpr double kXsSmallWork = 32.0 * 1024 * 1024;   // FP64 FMAs of one n x m x m product batch
 constexpr int kSiSmallBatch = 8;      // problems up to which the solve is latency bound
 constexpr double kSiFloorTol = 1e-10;  // residuals accepted once they stop decreasing
@@ -327,22 +328,77 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
         C[a * ld + b] = (float)Cin.at(z)[(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? sh : 0.0f);
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
-    // Right-looking, one barrier per column: every thread reads the pivot and
-    // row j (unchanged during step j), writes its share of R's row j and
-    // updates its share of the trailing block with the unscaled row.
-    for (int j = 0; j < m; ++j) {
-      const float piv = C[j * ld + j];
-      if (!(piv > 0.0f) || !isfinite(piv)) {
+    // Blocked right-looking factorisation, panels of kCholPanel columns and two
+    // barriers per panel: (a) every thread factors the panel's diagonal block
+    // U^T U = C_jj redundantly in registers (identical inputs, identical
+    // results, so a failed pivot stops every thread alike); (b) the panel's rows
+    // of R right of the block, U^T R_j,rest = C_j,rest, by forward substitution,
+    // one column per thread; (c) the trailing update C_rest -= R_j,rest^T R_j,rest.
+    for (int j0 = 0; j0 < m; j0 += kCholPanel) {
+      const int w = min(kCholPanel, m - j0);
+      float U[kCholPanel][kCholPanel];
+      float uinv[kCholPanel];
+      bool ok = true;
+#pragma unroll
+      for (int i = 0; i < kCholPanel; ++i) {
+        if (i < w && ok) {
+          float dd = C[(j0 + i) * ld + j0 + i];
+#pragma unroll
+          for (int k = 0; k < i; ++k) dd = fmaf(-U[k][i], U[k][i], dd);
+          if (!(dd > 0.0f) || !isfinite(dd)) {
+            ok = false;
+          } else {
+            const float ui = sqrtf(dd);
+            uinv[i] = 1.0f / ui;
+            U[i][i] = ui;
+#pragma unroll
+            for (int b = i + 1; b < kCholPanel; ++b) {
+              if (b < w) {
+                float v = C[(j0 + i) * ld + j0 + b];
+#pragma unroll
+                for (int k = 0; k < i; ++k) v = fmaf(-U[k][i], U[k][b], v);
+                U[i][b] = v * uinv[i];
+              }
+            }
+          }
+        }
+      }
+      if (!ok) {
         if (threadIdx.x == 0) bad = 1;
         break;
       }
-      const float ri = rsqrtf(piv);
-      for (int l = j + threadIdx.x; l < m; l += blockDim.x) R[j * ld + l] = C[j * ld + l] * ri;
-      const float r2 = ri * ri;
-      for (int a = j + 1 + ty; a < m; a += 16) {
-        const float ca = C[j * ld + a] * r2;
-        for (int b = a + tx; b < m; b += 16) C[a * ld + b] = fmaf(-ca, C[j * ld + b], C[a * ld + b]);
+      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int i = e / w, b = e % w;
+        if (b >= i) {
+          float v = 0.0f;
+#pragma unroll
+          for (int ii = 0; ii < kCholPanel; ++ii)
+#pragma unroll
+            for (int bb = 0; bb < kCholPanel; ++bb)
+              if (ii == i && bb == b) v = U[ii][bb];
+          R[(j0 + i) * ld + j0 + b] = v;
+        }
       }
+      for (int l = j0 + w + threadIdx.x; l < m; l += blockDim.x) {
+        float y[kCholPanel];
+#pragma unroll
+        for (int i = 0; i < kCholPanel; ++i) {
+          if (i < w) {
+            float v = C[(j0 + i) * ld + l];
+#pragma unroll
+            for (int k = 0; k < i; ++k) v = fmaf(-U[k][i], y[k], v);
+            y[i] = v * uinv[i];
+            R[(j0 + i) * ld + l] = y[i];
+          }
+        }
+      }
+      __syncthreads();
+      for (int a = j0 + w + ty; a < m; a += 16)
+        for (int b = a + tx; b < m; b += 16) {
+          float v = C[a * ld + b];
+          for (int i = 0; i < w; ++i) v = fmaf(-R[(j0 + i) * ld + a], R[(j0 + i) * ld + b], v);
+          C[a * ld + b] = v;
+        }
       __syncthreads();
     }
     __syncthreads();
@@ -440,15 +496,16 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol(PSet Cin, int m, doubl
 // The m/2 index pairs of a round are "slots"; slot I holds two whole rows of
 // the matrix (its top and bottom index) and belongs to one CTA (contiguous
 // slots per CTA).  A round: (1) every CTA computes the rotations of all slots
-// from a replicated table of their 2x2 diagonal blocks; (2) each CTA applies
-// every column rotation to the rows it holds and its own row rotations, which
-// is M'_{IJ} = J_I^T M_{IJ} J_J for all blocks of its rows (Eq. 6), and rotates
-// its share of the rows of V; (3) rows move to their next slot (tops one slot
+// from a replicated table of their 2x2 diagonal blocks; (2) one thread per 2x2
+// block of the CTA's rows applies both rotations at once,
+// M'_{IJ} = J_I^T M_{IJ} J_J (Eq. 6: the quad tile as the unit of work), and
+// (3) writes the four results to the slots their rows move to (tops one slot
 // down, bottoms one slot up, turning at both ends: the round-robin order in
-// which every pair meets once per sweep), and each moved row writes its entries
-// of the next round's 2x2 blocks into every CTA's table.  One cluster barrier
-// per round; since all CTAs see the same table, the sweep decision needs no
-// exchange.  Sweeps stop when no pair needs rotating (an off-diagonal entry is
+// which every pair meets once per sweep); each moved row also writes its
+// entries of the next round's 2x2 blocks into every CTA's table.  One cluster
+// barrier per round, split into arrive / wait so that each CTA rotates its
+// share of the rows of V while the others finish; since all CTAs see the same
+// table, the sweep decision needs no exchange.  Sweeps stop when no pair needs rotating (an off-diagonal entry is
 // rotated when it is above 2^-56 of the largest diagonal entry and not tiny
 // against its own diagonal pair), or after a sweep whose rotated entries were
 // all below 1e-8 relative (quadratic convergence).
@@ -477,7 +534,7 @@ __device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &
   s = t * c;
 }
 
-__global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, PSet theta, int *flag,
+__global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout, PSet theta, int *flag,
                                                    int *sweeps) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -492,15 +549,15 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
   double *rowsb = sh;
   auto ROW = [&](int buf, int slot, int tb) { return rowsb + (((size_t)buf * spc + (slot - s0)) * 2 + tb) * m; };
   double *V = rowsb + (size_t)2 * spc * 2 * m;              // vrows x m
-  double *ac = V + (size_t)vrows * m;                       // c of every slot
-  double *as = ac + half;                                   // s of every slot
+  double *ac = V + (size_t)vrows * m;                       // c of every slot, [round parity][slot]
+  double *as = ac + 2 * half;                               // s of every slot, same
   // angle inputs of every slot, replicated in every CTA, double-buffered by
   // round parity: [buf][slot][0 = h of the top row's index, 1 = h of the
   // bottom row's index, 2 = h_pq from the row of the smaller index]
-  double *nd = as + half;
+  double *nd = as + 2 * half;
   double *diag = nd + 2 * 3 * half;                         // m diagonal entries
-  int *ap = reinterpret_cast<int *>(diag + m);              // p of every slot
-  int *aq = ap + half;                                      // q of every slot
+  int *ap = reinterpret_cast<int *>(diag + m);              // p of every slot, [parity][slot]
+  int *aq = ap + 2 * half;                                  // q of every slot, same
   __shared__ int rotated;
   __shared__ unsigned int maxrel_bits;
   __shared__ double s_floor;
@@ -551,6 +608,10 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
       const int rr = r_global % (m - 1), rn = (r_global + 1) % (m - 1);
       const double *ndc = nd + (r_global & 1) * 3 * half;
       double *ndn_local = nd + ((r_global + 1) & 1) * 3 * half;
+      // this round's angle arrays (double-buffered by round parity: a thread may
+      // still rotate V with this round's angles while others start the next round)
+      double *acr = ac + (r_global & 1) * half, *asr = as + (r_global & 1) * half;
+      int *apr = ap + (r_global & 1) * half, *aqr = aq + (r_global & 1) * half;
       // (1) every CTA computes the angles of every slot from the replicated inputs
       for (int sl = threadIdx.x; sl < half; sl += blockDim.x) {
         const int u = top_index(sl, rr), v = bot_index(sl, rr);
@@ -566,77 +627,77 @@ __global__ void __launch_bounds__(512) k_si_jacobi(PSet Cin, int m, PSet Wout, P
           jacobi_angle(hpp, hqq, hpq, c, sv);
           rotated = 1;
         }
-        ac[sl] = c;
-        as[sl] = sv;
-        ap[sl] = p;
-        aq[sl] = q;
+        acr[sl] = c;
+        asr[sl] = sv;
+        apr[sl] = p;
+        aqr[sl] = q;
       }
       __syncthreads();
-      // (2a) every column rotation on the rows this CTA holds
-      const int nrow = (s1 - s0) * 2;
-      for (int e = threadIdx.x; e < nrow * half; e += blockDim.x) {
-        const int ri = e / half, J = e % half;
-        double *row = ROW(cur, s0 + (ri >> 1), ri & 1);
-        const int p = ap[J], q = aq[J];
-        const double x = row[p], y = row[q];
-        row[p] = ac[J] * x - as[J] * y;
-        row[q] = as[J] * x + ac[J] * y;
-      }
-      // V <- V J on the rows of V this CTA holds
-      for (int e = threadIdx.x; e < (v1 - v0) * half; e += blockDim.x) {
-        const int rl = e / half, J = e % half;
-        const int p = ap[J], q = aq[J];
-        const double x = V[rl * m + p], y = V[rl * m + q];
-        V[rl * m + p] = ac[J] * x - as[J] * y;
-        V[rl * m + q] = as[J] * x + ac[J] * y;
-      }
-      __syncthreads();
-      // (2b) row rotation of each own slot, written straight to the next slots;
-      // (3) tops move one slot down (slot 1's top to slot 0's bottom), bottoms one
-      // slot up (the last slot's bottom to its own top); slot 0's top stays.  A
-      // row that lands in a slot also publishes that slot's next-round angle
-      // inputs (its diagonal entry, and h_pq if it holds the smaller index) into
-      // every CTA's table.
-      double *nx[kCluster];
-      double *ndn[kCluster];
-#pragma unroll
-      for (int k = 0; k < kCluster; ++k) {
-        nx[k] = cluster.map_shared_rank(rowsb, k);
-        ndn[k] = cluster.map_shared_rank(ndn_local, k);
-      }
-      for (int e = threadIdx.x; e < (s1 - s0) * m; e += blockDim.x) {
-        const int sl = s0 + e / m, col = e % m;
+      // (2) the two-sided rotation of every 2x2 block held by this CTA, Eq. 6:
+      // M'_{IJ} = J_I^T M_{IJ} J_J for the row pair I of an own slot and every
+      // column pair J, in one pass; (3) the four results go straight to the slots
+      // their rows move to (tops one slot down, bottoms one slot up, slot 0's top
+      // fixed), and a row that lands in a slot also publishes that slot's
+      // next-round angle inputs (its diagonal entry, and h_pq if it holds the
+      // smaller index) into every CTA's table.  Remote addresses are mapped at
+      // each store (one mapa each) rather than held in registers.
+      for (int e = threadIdx.x; e < (s1 - s0) * half; e += blockDim.x) {
+        const int sl = s0 + e / half, J = e % half;
         const double *top = ROW(cur, sl, 0), *bot = ROW(cur, sl, 1);
-        const int p = ap[sl], q = aq[sl];
-        const int u = top_index(sl, rr);
-        const bool top_is_p = (u == p);
+        const int p = apr[sl], q = aqr[sl];
+        const bool top_is_p = (top_index(sl, rr) == p);
         const double *rp = top_is_p ? top : bot, *rq = top_is_p ? bot : top;
-        const double c = ac[sl], sv = as[sl];
-        double np = c * rp[col] - sv * rq[col];
-        double nq = sv * rp[col] + c * rq[col];
-        if (col == q) np = 0.0;      // the rotated pair is diagonal to rounding
-        if (col == p) nq = 0.0;
-        const double vals[2] = {top_is_p ? np : nq, top_is_p ? nq : np};   // new top, new bottom
+        const int pc = apr[J], qc = aqr[J];
+        const double cJ = acr[J], sJ = asr[J], c = acr[sl], sv = asr[sl];
+        // right factor J_J on the two rows
+        const double xp = rp[pc], yp = rp[qc], xq = rq[pc], yq = rq[qc];
+        const double p_pc = cJ * xp - sJ * yp, p_qc = sJ * xp + cJ * yp;
+        const double q_pc = cJ * xq - sJ * yq, q_qc = sJ * xq + cJ * yq;
+        // left factor J_I^T
+        double np_pc = c * p_pc - sv * q_pc, np_qc = c * p_qc - sv * q_qc;
+        double nq_pc = sv * p_pc + c * q_pc, nq_qc = sv * p_qc + c * q_qc;
+        if (J == sl) {          // the rotated pair's own block is diagonal to rounding
+          np_qc = 0.0;
+          nq_pc = 0.0;
+        }
         int dsl[2], dtb[2];
         if (sl == 0) { dsl[0] = 0; dtb[0] = 0; }          // slot 0's top is fixed
         else if (sl == 1) { dsl[0] = 0; dtb[0] = 1; }     // -> slot 0 bottom
         else { dsl[0] = sl - 1; dtb[0] = 0; }
         if (sl == half - 1) { dsl[1] = sl; dtb[1] = 0; } else { dsl[1] = sl + 1; dtb[1] = 1; }
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-          const int own = dsl[w] / spc;
-          double *base = nx[own] + ((((size_t)1 - cur) * spc + (dsl[w] - own * spc)) * 2 + dtb[w]) * m;
-          base[col] = vals[w];
-          const int nu = top_index(dsl[w], rn), nv = bot_index(dsl[w], rn);
-          const int idx = dtb[w] == 0 ? nu : nv, partner = dtb[w] == 0 ? nv : nu;
-          if (col == idx) {
-            for (int k = 0; k < kCluster; ++k) ndn[k][dsl[w] * 3 + dtb[w]] = vals[w];
-          } else if (col == partner && idx < partner) {
-            for (int k = 0; k < kCluster; ++k) ndn[k][dsl[w] * 3 + 2] = vals[w];
+        for (int h = 0; h < 2; ++h) {
+          const int col = h == 0 ? pc : qc;
+          const double np = h == 0 ? np_pc : np_qc, nq = h == 0 ? nq_pc : nq_qc;
+          const double vals[2] = {top_is_p ? np : nq, top_is_p ? nq : np};   // new top, new bottom
+#pragma unroll
+          for (int w = 0; w < 2; ++w) {
+            const int own = dsl[w] / spc;
+            double *base = cluster.map_shared_rank(rowsb, own) +
+                           ((((size_t)1 - cur) * spc + (dsl[w] - own * spc)) * 2 + dtb[w]) * m;
+            base[col] = vals[w];
+            const int nu = top_index(dsl[w], rn), nv = bot_index(dsl[w], rn);
+            const int idx = dtb[w] == 0 ? nu : nv, partner = dtb[w] == 0 ? nv : nu;
+            if (col == idx) {
+              for (int k = 0; k < kCluster; ++k)
+                cluster.map_shared_rank(ndn_local, k)[dsl[w] * 3 + dtb[w]] = vals[w];
+            } else if (col == partner && idx < partner) {
+              for (int k = 0; k < kCluster; ++k) cluster.map_shared_rank(ndn_local, k)[dsl[w] * 3 + 2] = vals[w];
+            }
           }
         }
       }
-      cluster.sync();
+      // the rows are in place once every CTA has arrived; meanwhile V <- V J on the
+      // rows of V this CTA holds (local, needs only the angles)
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      for (int e = threadIdx.x; e < (v1 - v0) * half; e += blockDim.x) {
+        const int rl = e / half, J = e % half;
+        const int pj = apr[J], qj = aqr[J];
+        const double x = V[rl * m + pj], y = V[rl * m + qj];
+        V[rl * m + pj] = acr[J] * x - asr[J] * y;
+        V[rl * m + qj] = asr[J] * x + acr[J] * y;
+      }
+      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
       cur ^= 1;
     }
     // every CTA saw the same angles: the sweep decision needs no exchange.
@@ -848,8 +909,8 @@ bool same(const PSet &a, const PSet &b) { return a.b0 == b.b0 && a.b1 == b.b1 &&
 size_t jacobi_smem(int m) {
   const int half = m / 2;
   const int spc = (half + kCluster - 1) / kCluster, vrows = (m + kCluster - 1) / kCluster;
-  return ((size_t)2 * spc * 2 * m + (size_t)vrows * m + 2 * half + 6 * half + m) * sizeof(double) +
-         (size_t)(2 * half) * sizeof(int) + 64;
+  return ((size_t)2 * spc * 2 * m + (size_t)vrows * m + 4 * half + 6 * half + m) * sizeof(double) +
+         (size_t)(4 * half) * sizeof(int) + 64;
 }
 size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
 size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + m) * sizeof(float); }
