@@ -562,6 +562,18 @@ def run_reference(args, world, rank):
                 "config": {"workload": "sweep256", "precision": "fp64 (CPU oracle)"},
                 "cpu_baseline": vals[-1],
                 "e2e": {"value": v, "unit": "RG-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.workload in ITEBD_WORKLOADS:
+        D = ITEBD_WORKLOADS[args.workload]
+        timed = itebd_cpu_baseline(d_values=(D,), budget_s=30.0)
+        v = timed["value_updates_per_s"][D]
+        return {"metric": ITEBD_METRIC, "value": v, "unit": "update steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / v, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "impl": "reference", "data": "synthetic (Neel start; no dataset)",
+                "config": {"workload": args.workload, "D_b": D, "precision": "fp64 (CPU oracle)"},
+                "cpu_baseline": {"value": v, "unit": "update steps/s", "cores": timed["cores"],
+                                 "kind": "oracle", "sample": timed["sample"]},
+                "e2e": {"value": v, "unit": "update steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if args.workload in QUANTUM_CONFIGS:
         q = QUANTUM_CONFIGS[args.workload]
         quantum_cpu_baseline(q, budget_s=0.0, max_steps=1)             # warm-up (untimed)
@@ -718,6 +730,73 @@ def itebd_cpu_baseline(d_values=(8, 16, 30), budget_s=4.0, warm=60):
                       f"{warm} warm-up updates"}
 
 
+ITEBD_METRIC = "iTEBD update steps/s, AF Heisenberg chain (tau = 0.05), FP64"
+ITEBD_WORKLOADS = {"itebd_heisenberg_d30": 30, "itebd_heisenberg_d16": 16}
+# kernels per warm-started update: phi GEMM, gate, rho GEMM, symmetrise (2), V^T rho V
+# (2 GEMMs + symmetrise (2)), Jacobi (copy, solve, take), Schmidt, V W GEMM, P' GEMM,
+# scale, take
+ITEBD_LAUNCHES_PER_UPDATE = 17
+
+
+def run_itebd_line(args, world, rank, local):
+    """One chain per rank (replicas): K timed updates after W warm-up updates, on
+    top of 300 untimed updates that bring the bond to D_b and the state near its
+    fixed point; CUDA events around the K updates on the library's stream."""
+    import torch
+    import paper_2602_05900_gb300 as pkg
+    pkg.load()
+    torch.cuda.set_device(local)
+    D = ITEBD_WORKLOADS[args.workload]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with pkg.Itebd([(1.0, 1.0, 0.05)], D, stream=stream) as c:
+        c.step(300 + args.warmup)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        barrier(world)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            a.record(stream)
+            c.step(args.steps)
+            b.record(stream)
+            b.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = reduce_max(a.elapsed_time(b), world)
+        e = float(c.energy()[0])
+    value = world * args.steps / (ms / 1e3)
+    out = {"metric": ITEBD_METRIC, "value": round(value, 3), "unit": "update steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (Neel start; no dataset)",
+           "config": {"workload": args.workload, "D_b": D, "tau": 0.05, "chains_per_gpu": 1,
+                      "l2": "per-update working set is tiny (< 1 MB); one flush before the timed region",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": {"kernel": "k_si_jacobi (cluster Jacobi of the 2D_b x 2D_b bond density matrix)",
+                        "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                        "traffic": None,
+                        "note": "one problem of size 2D_b on 8 SMs: bound by the per-round latency of the "
+                                "rotation-angle chain and the cluster barrier, not by a throughput peak"},
+           "energy_per_site": e, "energy_minus_bethe": e - (0.25 - math.log(2.0)),
+           "gpu_launches": ITEBD_LAUNCHES_PER_UPDATE * args.steps, "clocks": clk.summary()}
+    if rank == 0 and not args.quick:
+        cb = itebd_cpu_baseline(d_values=(D,), budget_s=min(args.cpu_budget, 10.0))
+        out["cpu_baseline"] = {"value": cb["value_updates_per_s"][D], "unit": "update steps/s",
+                               "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
+                               "blas": cb["blas"], "blas_threads": cb["blas_threads"]}
+        t0 = time.perf_counter()
+        with pkg.Itebd([(1.0, 1.0, 0.05)], D) as c2:
+            c2.step(200)
+            c2.energy()
+        out["e2e"] = {"value": round(200 / (time.perf_counter() - t0), 3), "unit": "update steps/s",
+                      "h2d_bytes_per_step": round((3 * 8 + 16 * 8 * 2) / 200, 3),
+                      "d2h_bytes_per_step": round(8 * 2 / 200, 3),
+                      "note": "create (couplings H2D) + 200 updates from the Neel state + energy (D2H)"}
+    return out
+
+
 def quantum_cpu_baseline(q, budget_s=20.0, max_steps=64):
     """The FP64 oracle (as it stands) on the host cores: imaginary-time Y steps
     of chain q at Dx = D_cut, timed until about budget_s of CPU work."""
@@ -821,7 +900,7 @@ def main():
     ap.add_argument("--steps", type=int, default=120)   # ~1 s timed at D=32: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="ising_044_d32",
-                    choices=sorted(CONFIGS) + ["sweep256"] + sorted(QUANTUM_CONFIGS))
+                    choices=sorted(CONFIGS) + ["sweep256"] + sorted(QUANTUM_CONFIGS) + sorted(ITEBD_WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "bf16x3", "bf16x6", "bf16xs"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU legs")
@@ -847,6 +926,8 @@ def main():
         out = run_sweep(args, world, rank, local)
     elif args.workload in QUANTUM_CONFIGS:
         out = run_quantum_line(args, world, rank, local)
+    elif args.workload in ITEBD_WORKLOADS:
+        out = run_itebd_line(args, world, rank, local)
     else:
         out = run_ours(args, world, rank, local)
     if rank == 0 and out is not None:

@@ -7,7 +7,9 @@
 //   phit  = g phi, theta = lam phit    k_itebd_gate
 //   rho   = theta^T theta              FP64 GEMM + symmetrise: the bond's right
 //                                      reduced density matrix (2D x 2D)
-//   Y, w  = eig(rho)                   cluster two-sided Jacobi (Sec. II.B, Eqs. 5-6)
+//   Y, w  = eig(rho)                   cluster two-sided Jacobi (Sec. II.B, Eqs. 5-6),
+//                                      warm-started from the same kind of bond's
+//                                      last eigenbasis V: eig(V^T rho V), Y = V W
 //   lam'  = sqrt(w[:D']) / norm        k_itebd_schmidt (+ the discarded weight)
 //   P'    = phit Y[:, :D'] / |s|       FP64 GEMM + k_itebd_scale (keeps the state
 //                                      normalised under the non-unitary gate)
@@ -161,6 +163,10 @@ struct hotrg_itebd {
   double *phi = nullptr, *phit = nullptr, *theta = nullptr, *rho = nullptr;
   double *gates = nullptr, *hs = nullptr, *disc = nullptr, *energy = nullptr, *trace = nullptr;
   double *rnorm = nullptr;
+  // warm start: the last full eigenbasis of each kind of bond (n x n column-major,
+  // n = nb[parity], -1 = none) and a buffer for the next one
+  double *Vb[2] = {nullptr, nullptr}, *Vn = nullptr;
+  int nb[2] = {-1, -1};
   double *si_work = nullptr;
   int *err = nullptr;
   std::vector<void *> allocs;
@@ -225,27 +231,56 @@ hotrg_status itebd_update(hotrg_itebd *c) {
                 c->rho, map1(n), map1(1), G, c->sM, c->sM, c->sM};
   ICK(c, gemm_f64(g2, st));
   ICK(c, symmetrize_trace(c->rho, n, c->sM, c->trace, 1, G, st));
-  // leading Dn eigenpairs of rho (all m eigenvalues for the discarded weight)
+  // Warm start: two updates ago the same kind of bond had eigenbasis V; near the
+  // fixed point rho is nearly diagonal in it, so the Jacobi runs on
+  // rho~ = V^T rho V (a few sweeps instead of ~11 from scratch) and the basis
+  // becomes V W.  phi and theta are free here and hold V^T-products.
+  const int par = (int)(c->nsteps & 1);
+  const bool warm = c->nb[par] == n;
+  double *Vold = c->Vb[par];
+  if (warm) {
+    // phi = rho V (row-major n x n), theta = V^T phi
+    MappedGemm w1{n, n, n, c->rho, map1(n), map1(1), Vold, map1(n), map1(1), c->phi, map1(n), map1(1),
+                  G, c->sM, c->sM, c->sM};
+    ICK(c, gemm_f64(w1, st));
+    MappedGemm w2{n, n, n, Vold, map1(n), map1(1), c->phi, map1(1), map1(n), c->theta, map1(n), map1(1),
+                  G, c->sM, c->sM, c->sM};
+    ICK(c, gemm_f64(w2, st));
+    ICK(c, symmetrize_trace(c->theta, n, c->sM, c->trace, 1, G, st));
+  }
+  // all n eigenpairs (the full basis is kept for the next warm start)
   SiBatch sb{};
   sb.P = G;
   sb.n = n;
-  sb.k = Dn;
+  sb.k = n;
   sb.m = jacobi_block(n);
-  sb.G = pset_linear(c->rho, c->sM);
+  sb.G = pset_linear(warm ? c->theta : c->rho, c->sM);
   long long nl = 0;
   ICK(c, jacobi_full(sb, c->si_work, st, &nl));
   const SiOut o = si_outputs(c->si_work, G, n, sb.m);
   k_itebd_schmidt<<<G, 64, 0, st>>>(o.theta, sb.m, Dn, c->l[iN], c->sL, c->disc, c->rnorm, c->err);
   ICK(c, cudaGetLastError());
-  // P' = phit Y, Q' = Y^T
+  // the new basis V' = V W (or W cold), column-major n x n, into Vn
   const long long ys = o.X.b1 - o.X.b0;
-  MappedGemm g3{kPhys * Dl, Dn, n, c->phit, map1(n), map1(1), o.X.b0, map1(n), map1(1), Pn, map1(Dn),
-                map1(1), G, c->sM, ys, c->sT};
+  if (warm) {
+    MappedGemm w3{n, n, n, Vold, map1(1), map1(n), o.X.b0, map1(n), map1(1), c->Vn, map1(1), map1(n),
+                  G, c->sM, ys, c->sM};
+    ICK(c, gemm_f64(w3, st));
+  } else {
+    k_itebd_take<<<dim3(grid1((long long)n * n), G), 256, 0, st>>>(o.X, (long long)n * n, c->Vn, c->sM);
+    ICK(c, cudaGetLastError());
+  }
+  std::swap(c->Vb[par], c->Vn);
+  c->nb[par] = n;
+  const PSet Y = pset_linear(c->Vb[par], c->sM);
+  // P' = phit Y / |s|, Q' = Y^T (Y = the leading Dn columns of the basis)
+  MappedGemm g3{kPhys * Dl, Dn, n, c->phit, map1(n), map1(1), Y.b0, map1(n), map1(1), Pn, map1(Dn),
+                map1(1), G, c->sM, c->sM, c->sT};
   ICK(c, gemm_f64(g3, st));
   k_itebd_scale<<<dim3(grid1((long long)kPhys * Dl * Dn), G), 256, 0, st>>>(Pn, (long long)kPhys * Dl * Dn,
                                                                            c->sT, c->rnorm);
   ICK(c, cudaGetLastError());
-  k_itebd_take<<<dim3(grid1((long long)Dn * n), G), 256, 0, st>>>(o.X, (long long)Dn * n, Qn, c->sT);
+  k_itebd_take<<<dim3(grid1((long long)Dn * n), G), 256, 0, st>>>(Y, (long long)Dn * n, Qn, c->sT);
   ICK(c, cudaGetLastError());
   // the next bond: (P, Q, lam) <- (Q', P', lam'); lam_other <- lam
   c->iP = iQn;
@@ -306,6 +341,8 @@ hotrg_status hotrg_itebd_create(int n, const double *couplings, int D_b, int D0,
       (s = ialloc(c, &c->gates, 16LL * n)) || (s = ialloc(c, &c->hs, 16LL * n)) ||
       (s = ialloc(c, &c->disc, (long long)n)) || (s = ialloc(c, &c->energy, 2LL * n)) ||
       (s = ialloc(c, &c->trace, (long long)n)) || (s = ialloc(c, &c->rnorm, (long long)n)) ||
+      (s = ialloc(c, &c->Vb[0], c->sM * n)) || (s = ialloc(c, &c->Vb[1], c->sM * n)) ||
+      (s = ialloc(c, &c->Vn, c->sM * n)) ||
       (s = ialloc(c, &c->si_work, si_workspace_doubles(n, (int)twoD, jacobi_block((int)twoD)))) ||
       (s = ialloc(c, &c->err, 4LL)))
     return bail(s);
