@@ -5,7 +5,8 @@
 // for B and C (see IdxMap).  64 x 64 output tile per 256-thread block, 4 x 4
 // outputs per thread, K staged through shared memory in chunks of 16 with a
 // register prefetch of the next chunk; grid.z runs over the instances of a batch.
-// GEMMs with at most 64 outputs and K >= 256 take a block-per-output dot kernel.
+// GEMMs with at most 64 outputs and K >= 256 take a block-per-output dot kernel,
+// GEMMs with M, N <= 128 a 16 x 16-tile kernel.
 #include "common.cuh"
 
 namespace hotrg {
@@ -151,6 +152,38 @@ __global__ void __launch_bounds__(NT) k_dot_f64(MappedGemm g) {
 
 constexpr long long kDotMaxOutputs = 64, kDotMinK = 256;
 
+// Small GEMMs (M, N <= 128): 16 x 16 output tiles, one output per thread, K in
+// chunks of 16 through shared memory.  A 64 x 64 tiling would put such a product
+// on at most four SMs, and GB300's FP64 rate per SM (about 2 FMA per clock) makes
+// the number of SMs, not the tile efficiency, the limit.
+constexpr int ST = 16;
+constexpr int kSmallMax = 128;
+
+__global__ void __launch_bounds__(256) k_gemm_f64_small(MappedGemm g) {
+  __shared__ double As[ST][ST + 1], Bs[ST][ST + 1];   // [k][row]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long long m0 = (long long)blockIdx.x * ST, n0 = (long long)blockIdx.y * ST;
+  g.A += blockIdx.z * g.bA;
+  g.B += blockIdx.z * g.bB;
+  g.C += blockIdx.z * g.bC;
+  // loads: thread (ty, tx) brings A(m0 + ty, k0 + tx) and B(n0 + ty, k0 + tx)
+  const long long ar = (m0 + ty < g.M) ? map_off(g.am, m0 + ty) : -1;
+  const long long br = (n0 + ty < g.N) ? map_off(g.bn, n0 + ty) : -1;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < g.K; k0 += ST) {
+    const int k = k0 + tx;
+    const bool kv = k < g.K;
+    As[tx][ty] = (ar >= 0 && kv) ? g.A[ar + map_off(g.ak, k)] : 0.0;
+    Bs[tx][ty] = (br >= 0 && kv) ? g.B[br + map_off(g.bk, k)] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ST; ++kk) acc = fma(As[kk][ty], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  const long long m = m0 + ty, n = n0 + tx;
+  if (m < g.M && n < g.N) g.C[map_off(g.cm, m) + map_off(g.cn, n)] = acc;
+}
+
 }  // namespace
 
 cudaError_t gemm_f64(const MappedGemm &g, cudaStream_t s) {
@@ -158,6 +191,13 @@ cudaError_t gemm_f64(const MappedGemm &g, cudaStream_t s) {
   if ((long long)g.M * g.N <= kDotMaxOutputs && g.K >= kDotMinK) {
     if (g.batch > 65535) return cudaErrorInvalidConfiguration;
     k_dot_f64<<<dim3((unsigned)(g.M * g.N), 1, (unsigned)(g.batch < 1 ? 1 : g.batch)), NT, 0, s>>>(g);
+    return cudaGetLastError();
+  }
+  if (g.M <= kSmallMax && g.N <= kSmallMax) {
+    if (g.batch > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 gs((unsigned)((g.M + ST - 1) / ST), (unsigned)((g.N + ST - 1) / ST),
+                  (unsigned)(g.batch < 1 ? 1 : g.batch));
+    k_gemm_f64_small<<<gs, 256, 0, s>>>(g);
     return cudaGetLastError();
   }
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
