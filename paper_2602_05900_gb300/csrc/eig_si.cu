@@ -524,13 +524,21 @@ __device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &
     t32 = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
   }
   double t = (double)t32;
+  // seed of c = (1 + t^2)^(-1/2) from the FP32 root, computed while t is refined
+  const float c32 = rsqrtf(fmaf(t32, t32, 1.0f));
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const double F = fma(fma(g, t, diff), t, -g);   // g t^2 + diff t - g
     const double dF = fma(2.0 * g, t, diff);
     t -= F * (double)__frcp_rn((float)dF);
   }
-  c = rsqrt_fp64(fma(t, t, 1.0));
+  // |t| <= 1 (the smaller root), so x = 1 + t^2 lies in [1, 2] and needs no
+  // power-of-two scaling: two Newton steps y <- y (3 - x y^2) / 2 in FP64
+  const double x = fma(t, t, 1.0);
+  double y = (double)c32;
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  c = y;
   s = t * c;
 }
 
