@@ -756,6 +756,10 @@ __global__ void __launch_bounds__(256) k_si_rotate(PSet A, PSet W, PSet Out, int
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const int jend = tri ? min(m, c0 + 32) : m;
+  // skip the zero-padded tail of the last j-chunk and the groups of 8 columns
+  // that start past m (uniform per block; their loads are zero-filled, so only
+  // work is skipped; at m = 72 the padding was 44 % of the FMAs)
+  const int ugroups = min(4, (m - c0 + 7) / 8);
   for (int j0 = 0; j0 < jend; j0 += 32) {
     for (int e = threadIdx.x; e < 32 * 32; e += 256) {
       const int jj = e >> 5, ii = e & 31;
@@ -766,11 +770,13 @@ __global__ void __launch_bounds__(256) k_si_rotate(PSet A, PSet W, PSet Out, int
       Ws[ii][jj] = (jw < m && cc < m) ? w[(size_t)cc * m + jw] : 0.0;
     }
     __syncthreads();
+    const int jn = min(32, jend - j0);
 #pragma unroll 8
-    for (int jj = 0; jj < 32; ++jj) {
+    for (int jj = 0; jj < jn; ++jj) {
       const double av = As[jj][tx];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = fma(av, Ws[jj][ty + 8 * u], acc[u]);
+      for (int u = 0; u < 4; ++u)
+        if (u < ugroups) acc[u] = fma(av, Ws[jj][ty + 8 * u], acc[u]);
     }
     __syncthreads();
   }
