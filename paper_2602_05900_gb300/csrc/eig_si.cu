@@ -264,32 +264,43 @@ __global__ void k_si_gram_reduce(PSet Cp, PSet C, int nchunks, int m, int sym, i
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     double sv;
     if (sym) {
-      // (a, b) lives in tile (a / U, b / U); a tile below the diagonal was skipped
+      // (a, b) lives in tile (a / U, b / U); a tile below the diagonal was skipped.
+      // Eight independent partial sums keep eight loads in flight (the chunk
+      // sums are load-latency bound), combined in a fixed order.
       const bool upper = (a / U) <= (b / U);
       const long long off = upper ? (long long)a * m + b : (long long)b * m + a;
+      double v4 = 0.0, v5 = 0.0, v6 = 0.0, v7 = 0.0;
       int c = 0;
-      for (; c + 4 <= nchunks; c += 4) {
+      for (; c + 8 <= nchunks; c += 8) {
         v0 += src[c * mm + off];
         v1 += src[(c + 1) * mm + off];
         v2 += src[(c + 2) * mm + off];
         v3 += src[(c + 3) * mm + off];
+        v4 += src[(c + 4) * mm + off];
+        v5 += src[(c + 5) * mm + off];
+        v6 += src[(c + 6) * mm + off];
+        v7 += src[(c + 7) * mm + off];
       }
       for (; c < nchunks; ++c) v0 += src[c * mm + off];
-      sv = (v0 + v1) + (v2 + v3);
+      sv = ((v0 + v1) + (v2 + v3)) + ((v4 + v5) + (v6 + v7));
     } else {
-      double w0 = 0.0, w1 = 0.0;
+      double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
       int c = 0;
-      for (; c + 2 <= nchunks; c += 2) {
+      for (; c + 4 <= nchunks; c += 4) {
         v0 += src[c * mm + a * m + b];
         w0 += src[c * mm + b * m + a];
         v1 += src[(c + 1) * mm + a * m + b];
         w1 += src[(c + 1) * mm + b * m + a];
+        v2 += src[(c + 2) * mm + a * m + b];
+        w2 += src[(c + 2) * mm + b * m + a];
+        v3 += src[(c + 3) * mm + a * m + b];
+        w3 += src[(c + 3) * mm + b * m + a];
       }
       for (; c < nchunks; ++c) {
         v0 += src[c * mm + a * m + b];
         w0 += src[c * mm + b * m + a];
       }
-      sv = 0.5 * ((v0 + v1) + (w0 + w1));
+      sv = 0.5 * (((v0 + v1) + (v2 + v3)) + ((w0 + w1) + (w2 + w3)));
     }
     if (ns) sv = (a == b ? 1.5 : 0.0) - 0.5 * sv;
     C.at(z)[a * m + b] = sv;
