@@ -160,6 +160,20 @@ def test_batch_of_couplings(pkg):
         assert abs(v / want - 1) < 1e-12, c
 
 
+def test_batch_two_cut_groups(pkg):
+    """Chains with different cuts form separate groups of one context; the time
+    trace closes every group.  (Heisenberg at D_cut 16 cuts in spectral gaps; the
+    Ising chain's cut at 12 only drops exact zeros.)"""
+    cases = [((1.0, 1.0, 1 / 32), 16), ((0.0, 1.0, 0.1), 12), ((1.0, 1.0, 1 / 32), 16)]
+    nt, nx = 5, 8
+    with pkg.HotrgBatch([pkg.xxz_tensor(*c) for c, _ in cases], [d for _, d in cases], "fp64") as b:
+        b.run_quantum(nt, nx)
+        got = b.ln_z_per_site()
+    for (c, d), v in zip(cases, got):
+        want = hz.run(hz.cell_tensor(*c), d, nt, nx).ln_z_per_site
+        assert abs(v / want - 1) < 1e-12, (c, d)
+
+
 def test_free_energy_low_temperature(pkg):
     """beta = 16 at D_cut = 32 on the FP64 path: f approaches the Bethe-ansatz
     ground-state energy 1/4 - ln 2 with the T^2 / 3 correction of the chain."""
