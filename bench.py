@@ -564,7 +564,7 @@ def run_reference(args, world, rank):
                 "e2e": {"value": v, "unit": "RG-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if args.workload in ITEBD_WORKLOADS:
         D = ITEBD_WORKLOADS[args.workload]
-        timed = itebd_cpu_baseline(d_values=(D,), budget_s=30.0)
+        timed = itebd_cpu_baseline(d_values=(D,), budget_s=min(30.0, 0.25 * max(1, args.steps)))
         v = timed["value_updates_per_s"][D]
         return {"metric": ITEBD_METRIC, "value": v, "unit": "update steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / v, 4),

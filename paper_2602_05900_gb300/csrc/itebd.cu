@@ -214,9 +214,13 @@ hotrg_status itebd_update(hotrg_itebd *c) {
   const int G = c->G, Dl = c->outer, Dm = c->mid, Dr = c->outer;
   const int n = kPhys * Dr, Dn = std::min(c->Db, std::min(kPhys * Dl, kPhys * Dr));
   double *P = c->t[c->iP], *Q = c->t[c->iQ];
+  // the two tensor buffers not holding P or Q receive P' and Q'
   int iPn = -1, iQn = -1;
-  for (int k = 0; k < 4; ++k)
-    if (k != c->iP && k != c->iQ) (iPn < 0 ? iPn : iQn) = k;
+  for (int k = 0; k < 4; ++k) {
+    if (k == c->iP || k == c->iQ) continue;
+    if (iPn < 0) iPn = k;
+    else iQn = k;
+  }
   double *Pn = c->t[iPn], *Qn = c->t[iQn];
   const int iN = 3 - c->iL - c->iO;
   // phi = P Q

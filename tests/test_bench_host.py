@@ -65,6 +65,21 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
 
 
+@pytest.mark.parametrize("workload,unit", [("heisenberg_b4_d8", "update steps/s"),
+                                           ("itebd_heisenberg_d16", "update steps/s")])
+def test_reference_arm_quantum_workloads(workload, unit):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", workload, "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == unit
+    assert d["config"]["workload"] == workload
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
 def test_transient_steps_schedule():
     import bench
     # each step squares the fused dimension (capped at D_cut): 2 -> 4 -> 16 -> D_cut
