@@ -663,8 +663,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
       for (int e = threadIdx.x; e < (s1 - s0) * half; e += blockDim.x) {
         const int sl = s0 + e / half, J = e % half;
         const double *top = ROW(cur, sl, 0), *bot = ROW(cur, sl, 1);
-        const int p = apr[sl], q = aqr[sl];
-        const bool top_is_p = (top_index(sl, rr) == p);
+        const bool top_is_p = (top_index(sl, rr) == apr[sl]);
         const double *rp = top_is_p ? top : bot, *rq = top_is_p ? bot : top;
         const int pc = apr[J], qc = aqr[J];
         const double cJ = acr[J], sJ = asr[J], c = acr[sl], sv = asr[sl];
