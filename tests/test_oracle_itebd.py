@@ -81,6 +81,39 @@ def test_state_stays_normalised_over_long_runs():
     assert 1e-3 < np.linalg.norm(st.P) < 1e3
 
 
+def _update_via_density_matrix(P, Q, lam, g, D_b):
+    """The same update with the SVD taken from the eigendecomposition of theta^T theta
+    (the bond's right density matrix: the Hermitian route of the GPU path)."""
+    Dl, d, _ = P.shape
+    Dr = Q.shape[2]
+    phit = np.einsum("ABab,iabm->iABm", g.reshape(d, d, d, d), np.einsum("iaj,jbm->iabm", P, Q))
+    theta = (lam[:, None, None, None] * phit).reshape(Dl * d, d * Dr)
+    w, V = np.linalg.eigh(theta.T @ theta)
+    w, V = np.maximum(w[::-1], 0.0), V[:, ::-1]
+    Dn = min(D_b, w.size)
+    s = np.sqrt(w[:Dn])
+    norm = np.linalg.norm(s)
+    Y = V[:, :Dn]
+    return (Y.T.reshape(Dn, d, Dr), (phit.reshape(Dl * d, d * Dr) @ Y).reshape(Dl, d, Dn) / norm,
+            s / norm)
+
+
+def test_density_matrix_route_matches_svd_route():
+    # 1500 updates from the Neel state at D_b = 16: the two routes to the Schmidt
+    # decomposition give the same energy to well below the truncation level
+    g = hz.bond_gate(1.0, 1.0, 0.05)
+    h = hz.bond_hamiltonian(1.0, 1.0)
+    st = it.run(1.0, 1.0, 0.05, 16, 1500)
+    P, Q, lam = it.neel_state()
+    other = np.ones(1)
+    for _ in range(1500):
+        old = lam
+        P, Q, lam = _update_via_density_matrix(P, Q, lam, g, 16)
+        other = old
+    e_gram = 0.5 * (it.bond_energy(P, Q, lam, h) + it.bond_energy(Q, P, other, h))
+    assert abs(e_gram - it.site_energy(st, h)) < 1e-8
+
+
 def test_energy_falls_with_bond_dimension():
     h = hz.bond_hamiltonian(1.0, 1.0)
     es = [it.site_energy(it.run(1.0, 1.0, 0.05, D, 1500), h) for D in (2, 4, 8, 16)]
