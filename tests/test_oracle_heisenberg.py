@@ -148,6 +148,21 @@ def test_xx_chain_thermodynamic_limit(n_time, D_cut, tol):
     assert abs(r.ln_z_per_site - hz.xx_trotter_ln_z_per_cell(1.0, tau, 2 ** n_time)) < tol
 
 
+def test_open_time_legs_lose_the_entropy():
+    """Why the time direction is closed before the chain steps: X steps taken with
+    the time legs open truncate the time-boundary states, and for the Ising chain
+    (Jxy = 0, beta Jz / 4 = 0.4) only the ground-state term survives,
+    ln Z / L = beta Jz / 4 instead of ln(2 cosh(beta Jz / 4))."""
+    tau, nt, nx = 0.1, 4, 24
+    T0 = hz.cell_tensor(0.0, 1.0, tau)
+    opened = hotrg.run(T0, 16, nt + nx, dirs=["y"] * nt + ["x"] * nx).ln_z_per_site
+    closed = hz.run(T0, 16, nt, nx).ln_z_per_site
+    beta, M = tau * 2 ** nt, 2 ** nt
+    assert abs(closed - hz.ising_chain_ln_z_per_cell(1.0, beta, M)) < 1e-13
+    assert abs(opened * M / 2 - beta / 4) < 1e-6            # per site: ground state only
+    assert closed - opened > 0.04                            # the missing entropy per cell
+
+
 @pytest.mark.parametrize("Jz", [1.0, -1.0, 2.5])
 def test_ising_chain_limit(Jz):
     tau, nt = 0.1, 4
