@@ -40,8 +40,7 @@ from workloads import CONFIGS, QUANTUM_CONFIGS, sweep256  # noqa: E402
 
 METRIC = "HOTRG RG-steps/s at steady-state D=D_cut (TF32 tensor-core contractions, FP64 eig)"
 SWEEP_METRIC = "HOTRG aggregate RG-steps/s, batched beta sweep (instance-steps/s, TF32 contractions, FP64 eig)"
-EIG_NOTE = ("fp64 batched subspace iteration + two-sided Jacobi Rayleigh-Ritz (top D'+1 pairs, "
-            "both sides), cuSOLVER syevdx fallback")
+EIG_NOTE = "fp64 batched subspace iteration + two-sided Jacobi Rayleigh-Ritz (top D'+1 pairs, both sides)"
 L2_FLUSH_BYTES = 512 << 20
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor throughput
 # BF16 tensor-core products per algorithmic product: split planes, or for the
@@ -111,22 +110,38 @@ def golden(name):
     return None
 
 
+def gpu_selector(local: int) -> str:
+    """nvidia-smi's identifier of the GPU this rank drives.  nvidia-smi numbers
+    GPUs physically and ignores CUDA_VISIBLE_DEVICES, so the device is named by
+    its UUID (from torch), else by the local-th entry of CUDA_VISIBLE_DEVICES."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u:
+            return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    except Exception:
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return vis[local] if local < len(vis) else str(local)
+
+
 class ClockSampler:
-    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    """Samples SM clocks and throttle reasons of one GPU with nvidia-smi (every
+    50 ms) while running."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, local: int):
+        self.gpu = gpu_selector(local)
         self.proc = None
         self.lines = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
-                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", self.gpu], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -146,7 +161,7 @@ class ClockSampler:
                 self.proc.kill()
             self.t.join(timeout=2)
 
-    def summary(self):
+    def summary(self, ms_per_step=None):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -161,8 +176,13 @@ class ClockSampler:
             for nm, v in zip(names, parts[3:7]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        med = statistics.median(sm) if sm else None
+        out = {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+               "gpu": self.gpu, "interval_ms": 50}
+        if med and ms_per_step:
+            # time x median clock: SM cycles per step (comparable across clock levels)
+            out["mcycles_per_step"] = round(ms_per_step * med / 1e3, 4)
+        return out
 
 
 def initial_tensor(pkg, cfg):
@@ -216,6 +236,117 @@ def full_job_lnz(pkg, cfg, precision, stream):
         return h.ln_z_per_site()
 
 
+def measure_peaks(torch):
+    """Dense-GEMM throughput of this GPU measured here with the vendor library
+    (cuBLAS through torch.matmul, best of several runs, CUDA events): TF32
+    (FP32 inputs with TF32 tensor-core math, 8192^3) and FP64 (4096^3).  They
+    are the denominators of the TF32 contraction kernels' and the FP64
+    eigensolver's fractions."""
+    out = {"how": "torch.matmul (cuBLAS), CUDA events, best of 10 (TF32, 8192^3) / 3 (FP64, 4096^3)"}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = True
+        for name, dt, n, reps in (("tf32_tflops", torch.float32, 8192, 10), ("fp64_tflops", torch.float64, 4096, 3)):
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            torch.matmul(a, b)
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = round(2.0 * n ** 3 / (best / 1e3) / 1e12, 2)
+            del a, b
+    except Exception as ex:      # reported, never fatal
+        out["error"] = str(ex)[:200]
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        torch.cuda.empty_cache()
+    return out
+
+
+def tensor_peak(prec, bf16_burst, peak_src, measured):
+    """(peak TFLOP/s, description) of a contraction in precision mode prec."""
+    if prec == "tf32":
+        if measured.get("tf32_tflops"):
+            return measured["tf32_tflops"], "TF32 dense GEMM measured in this run (cuBLAS 8192^3, best of 10)"
+        return bf16_burst * TF32_PER_BF16, f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"
+    if prec in BF16_SPLIT_PRODUCTS:
+        n = BF16_SPLIT_PRODUCTS[prec]
+        return bf16_burst / n, f"{peak_src} bf16 burst / {n} products (algorithmic flops)"
+    if measured.get("fp64_tflops"):
+        return measured["fp64_tflops"], "FP64 dense GEMM measured in this run (cuBLAS 4096^3)"
+    return 1.25, "nominal FP64"
+
+
+def steady_state_tensor(pkg, cfg, prec, stream):
+    """The normalised tensor of a job at Dx = Dy = D_cut (host copy) and the
+    direction of its next step."""
+    h, d = steady_job(pkg, cfg, prec, stream)
+    T = h.tensor()
+    h.close()
+    return T, d
+
+
+def e2e_steady(pkg, cfg, prec, torch, stream, k):
+    """The same steady-state steps as the device-timed value, end to end
+    through the C ABI from host memory: the steady-state tensor (pinned host
+    buffer) -> hotrg_create (H2D and all allocations) -> k steps -> ln Z / N
+    (D2H), timed on the host around the whole sequence, best of two."""
+    T, d = steady_state_tensor(pkg, cfg, prec, stream)
+    pinned = torch.empty(T.size, dtype=torch.float64, pin_memory=True)
+    host = pinned.numpy().reshape(T.shape)
+    host[...] = T
+    best = None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with pkg.Hotrg(host, cfg.D_cut, prec, stream) as h:
+            dd = d
+            for _ in range(k):
+                h.step(dd)
+                dd = "y" if dd == "x" else "x"
+            lz = h.ln_z_per_site()
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    # device -> host per step: the step's error flag (4 B) and, per convergence
+    # check of the eigensolver (about 1.5 per step), the residuals, Ritz values
+    # and status of both environments (2 (k + m) doubles + 16 B)
+    kk, m = cfg.D_cut + 1, min(96, ((2 * (cfg.D_cut + 1) + 7) // 8) * 8)
+    d2h_step = 4 + 1.5 * (16 * (kk + m) + 16)
+    return {"value": round(k / best, 4), "unit": "RG-steps/s",
+            "h2d_bytes_per_step": round(T.size * 8 / k, 2),
+            "d2h_bytes_per_step": round(d2h_step + 8 * 5 / k, 2),
+            "ln_z_finite": bool(math.isfinite(lz)),
+            "note": f"{k} steady-state steps at D = {cfg.D_cut} (the steps the value times): create from "
+                    f"the pinned host tensor (H2D, allocations), the steps, ln Z / N (D2H); host clock, "
+                    f"best of 2"}
+
+
+def eig_block(prof, steps, D, measured, info):
+    """The eigensolver stage against the least work a dense FP64 symmetric
+    eigensolver needs for the two environments (Householder tridiagonalisation,
+    2 x 4/3 n^3 flops at n = D^2) at the FP64 rate measured here."""
+    n = D * D
+    ms = prof["ms"]["eig"] / max(1, steps)
+    dense = 2 * (4.0 / 3.0) * n ** 3
+    fp64 = measured.get("fp64_tflops") or 1.0
+    iters = [i.eig_iters for i in info if i.eig_path == 2]
+    return {"ms_per_step": round(ms, 4), "share_of_step": None,
+            "n": n, "pairs_per_side": D + 1,
+            "subspace_iterations_per_step": round(statistics.mean(iters), 2) if iters else None,
+            "dense_fp64_tridiagonalisation_flops": dense,
+            "dense_fp64_lower_bound_ms": round(dense / (fp64 * 1e12) * 1e3, 4),
+            "fp64_peak_tflops": fp64,
+            "note": "the solver does FP64-grade products on the BF16 tensor cores (exact slices) and "
+                    "latency-bound small factorisations; its time is compared with what a dense FP64 "
+                    "tridiagonalisation of both environments would need at the measured FP64 rate"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2602_05900_gb300 as pkg
@@ -225,9 +356,11 @@ def run_ours(args, world, rank, local):
     prec = args.precision or cfg.precision
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    measured = measure_peaks(torch) if rank == 0 else {}
 
     h, d = steady_job(pkg, cfg, prec, stream, autotune=not args.no_autotune)
     _, d = time_steps(torch, h, d, args.warmup, stream, flush)
+    n_before = h.dims()[2]
     h.profile_enable(True)
     torch.cuda.synchronize()
     barrier(world)
@@ -237,6 +370,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     prof = h.profile_read()
+    info = [h.step_info(i) for i in range(n_before, h.dims()[2])]
     h.close()
     total_ms = sum(times)
     max_ms = reduce_max(total_ms, world)
@@ -250,23 +384,20 @@ def run_ours(args, world, rank, local):
     q_ms = prof["ms"]["proj_q"] / max(1, prof["stage_launches"]["proj_q"])
     q_flops = 2.0 * D ** 7
     achieved = q_flops / (q_ms / 1e3) / 1e12
-    if prec == "tf32":
-        peak, peak_note = bf16_burst * TF32_PER_BF16, f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"
-    elif prec in BF16_SPLIT_PRODUCTS:
-        peak = bf16_burst / BF16_SPLIT_PRODUCTS[prec]
-        peak_note = f"{peak_src} bf16 burst / {BF16_SPLIT_PRODUCTS[prec]} products (algorithmic flops)"
-    else:
-        peak, peak_note = 1.25, "nominal FP64 (no measured FP64 peak)"
+    peak, peak_note = tensor_peak(prec, bf16_burst, peak_src, measured)
     roofline = {"kernel": "k_tc_gemm a6 bond contraction Q=P.T" if prec != "fp64" else "k_gemm_f64 a6",
                 "bound": "tensor" if prec != "fp64" else "alu", "achieved": round(achieved, 2),
                 "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "traffic": captured_traffic(cfg.name, prec), "traffic_unit": "bytes/launch",
                 "algorithmic_bytes": 4 * (D ** 5 + D ** 4 + D ** 5) if prec == "tf32" else None,
                 "peak_source": peak_note,
+                "frac_of_nominal_tf32_from_bf16": round(achieved / (bf16_burst * TF32_PER_BF16), 4)
+                if prec == "tf32" else None,
                 "flops_per_launch": q_flops, "ms_per_launch": round(q_ms, 5)}
 
+    ms_step = max_ms / args.steps
     out = {"metric": METRIC, "value": round(value, 4), "unit": "RG-steps/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": {"tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6", "fp64": "f64",
                      "bf16xs": "bf16 (exact slices, FP64-grade)"}[prec],
@@ -278,15 +409,16 @@ def run_ours(args, world, rank, local):
                             f"per-step working set > L2", "parallelism": f"replicas x{world}"},
            "tflops": round(flops_step * world * args.steps / (max_ms / 1e3) / 1e12, 3),
            "roofline": roofline,
+           "measured_peaks": measured,
            "stage_ms_per_step": {k: round(v / max(1, prof["steps"]), 4) for k, v in prof["ms"].items()},
            "gpu_launches": int(prof["launches"]),
-           "clocks": clk.summary()}
+           "clocks": clk.summary(ms_step)}
     out["stage_share"] = {k: round(v / max(1e-9, sum(prof["ms"].values())), 4) for k, v in prof["ms"].items()}
     out["eig_share"] = out["stage_share"]["eig"]
-    out["dominant_by_time"] = {"stage": "eig", "share": out["eig_share"], "bound": "latency",
-                               "note": "FP64 eigensolver (cluster Jacobi Rayleigh-Ritz, CholeskyQR, "
-                                       "rotations): dependent FP64 chains and cluster barriers; the "
-                                       "roofline above is the dominant contraction kernel"}
+    out["eig"] = eig_block(prof, prof["steps"], D, measured, info)
+    out["eig"]["share_of_step"] = out["eig_share"]
+    out["dominant_by_time"] = {"stage": max(out["stage_share"], key=out["stage_share"].get),
+                               "share": max(out["stage_share"].values())}
 
     if rank == 0 and not args.quick:
         # accuracy of the full job against the FP64 oracle (stored by tests/golden/make_oracle_values.py)
@@ -305,14 +437,81 @@ def run_ours(args, world, rank, local):
         v64 = len(t64) / (sum(t64) / 1e3)
         out["fp64_gpu_value"] = round(v64, 4)
         out["speedup_vs_fp64_gpu"] = round(value / world / v64, 3)
-        out["e2e"] = e2e(pkg, cfg, prec, torch)
+        out["e2e"] = e2e_steady(pkg, cfg, prec, torch, stream, args.steps)
+        out["e2e_job"] = e2e(pkg, cfg, prec, torch)
         out["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
         out["cpu_baseline_1_thread"] = cpu_baseline_single_thread(cfg)
+        out["vs_cpu_same_precision"] = {
+            "fp64_gpu_over_oracle": round(v64 / out["cpu_baseline"]["value"], 3),
+            "note": "the plain FP64 GPU path against the FP64 oracle on the host cores (same arithmetic); "
+                    "the headline value is TF32 contractions and is not a same-precision comparison"}
+        out["fp64_grade"] = fp64_grade_block(pkg, stream, torch, flush, measured)
+        out["sweep"] = sweep_block(pkg, torch, flush, measured, bf16_burst, peak_src)
         out["precision_modes"] = precision_modes(pkg, stream, torch)
         out["quantum_chain"] = quantum_report(pkg, stream, torch, flush)
         out["itebd"] = itebd_report(pkg, torch)
         out["itebd"]["cpu_baseline"] = itebd_cpu_baseline()
     return out
+
+
+def fp64_grade_block(pkg, stream, torch, flush, measured):
+    """The free-energy target (<= 1e-9 relative at D_cut = 48) with its speed-up
+    over the plain FP64 GPU path on the same inputs: steady-state RG-steps/s of
+    the exact-slice mode (BF16 tensor cores, FP64-grade) and of the FP64 path at
+    D_cut = 32 (beta 0.44) and 48 (beta 0.44, h 0.01), and each full job's
+    relative ln Z / N error against the stored FP64 oracle value."""
+    res = {"note": "steady-state steps at Dx = Dy = D_cut (CUDA events, L2 flushed before each); errors "
+                   "of whole jobs (30 steps) against the stored FP64 oracle"}
+    for name in ("ising_044_d32", "ising_044h_d48"):
+        cfg = CONFIGS[name]
+        g = golden(name)
+        row = {}
+        for prec, k in (("bf16xs", 6), ("fp64", 3)):
+            h, d = steady_job(pkg, cfg, prec, stream)
+            time_steps(torch, h, d, 1, stream, flush)
+            t, _ = time_steps(torch, h, d, k, stream, flush)
+            h.close()
+            v = len(t) / (sum(t) / 1e3)
+            lz = full_job_lnz(pkg, cfg, prec, stream)
+            row[prec] = {"rg_steps_per_s": round(v, 3), "ms_per_step": round(sum(t) / len(t), 3),
+                         "fe_rel_err_vs_fp64_oracle": abs(lz / g["ln_z_per_site"] - 1) if g else None}
+        row["speedup_bf16xs_over_fp64_gpu"] = round(row["bf16xs"]["rg_steps_per_s"] /
+                                                    row["fp64"]["rg_steps_per_s"], 3)
+        res[f"D{cfg.D_cut}"] = row
+    return res
+
+
+def sweep_block(pkg, torch, flush, measured, bf16_burst, peak_src, steps=3):
+    """The batched beta sweep (256 instances, D_cut 16-40, TF32) inside the
+    default run: aggregate instance-steps/s over `steps` steady batch steps."""
+    models = sweep256()
+    stream = torch.cuda.Stream()
+    n = len(models)
+    ntr = max(transient_steps(2, m.D_cut) for m in models)
+    bt = sweep_batch(pkg, models, "tf32", stream)
+    d = "x"
+    for _ in range(ntr):
+        bt.step(d)
+        d = "y" if d == "x" else "x"
+    _, d = time_steps(torch, bt, d, 2, stream, flush)
+    bt.profile_enable(True)
+    times, d = time_steps(torch, bt, d, steps, stream, flush)
+    prof = bt.profile_read()
+    bt.close()
+    ms = sum(times)
+    q_flops = sum(2.0 * m.D_cut ** 7 for m in models)
+    q_ms = prof["ms"]["proj_q"] / max(1, prof["steps"])
+    peak, note = tensor_peak("tf32", bf16_burst, peak_src, measured)
+    share = {k: round(v / max(1e-9, sum(prof["ms"].values())), 4) for k, v in prof["ms"].items()}
+    return {"workload": "sweep256: 256 Ising instances, beta ~ U[0.35, 0.55], D_cut in {16, 24, 32, 40}, TF32",
+            "value": round(n * steps / (ms / 1e3), 3), "unit": "RG-steps/s (instance-steps/s)",
+            "ms_per_batch_step": round(ms / steps, 3), "steps_timed": steps,
+            "roofline": {"kernel": "k_tc_gemm a6 (all cut groups of a step)", "bound": "tensor",
+                         "achieved": round(q_flops / (q_ms / 1e3) / 1e12, 2), "peak": round(peak, 1),
+                         "unit": "TFLOP/s", "frac": round(q_flops / (q_ms / 1e3) / 1e12 / peak, 4),
+                         "peak_source": note},
+            "stage_share": share, "eig_share": share["eig"], "gpu_launches_per_step":
+            round(prof["launches"] / max(1, prof["steps"]), 1)}
 
 
 def precision_modes(pkg, stream, torch):

@@ -98,7 +98,7 @@ typedef struct {
                        +inf when nothing is cut                                     */
   double trace_G;   /* Tr G_L (= ||M||_F^2)                                        */
   int eig_path;     /* eigensolver used: 0 none (no cut), 1 direct Jacobi,
-                       2 subspace iteration, 3 library fallback (cuSOLVER syevdx)   */
+                       2 subspace iteration                                         */
   int eig_iters;    /* subspace iterations (path 2)                                */
   double eig_residual; /* max_i<=D' ||G u_i - lambda_i u_i|| / lambda_1 (path 2)    */
 } hotrg_step_info_t;
@@ -215,10 +215,14 @@ void hotrg_itebd_destroy(hotrg_itebd *ctx);
 /*
  * Create a context holding T0 (host, D0^4 doubles, [x,x',y,y'] row-major,
  * borrowed and copied) scaled by its max-norm, ready for steps with cut D_cut.
+ * T0 is the local tensor of Sec. II.A, Eq. 2 (Z = Tr T^N): the network of N
+ * copies of it is the partition function the steps coarse-grain; c_0 = max|T0|
+ * starts the FP64 log-sum with weight 1 (one site).
  * stream: a cudaStream_t (NULL = the legacy default stream); the context
  * enqueues all its work there.  All device memory for steps up to D_cut is
  * allocated here (HOTRG_ENOMEM if it does not fit).  On failure *out is set to
- * NULL.  Requires 1 <= D0 <= 64, 1 <= D_cut <= 64.
+ * NULL.  Requires 1 <= D0 <= 64, 1 <= D_cut <= 64; a T0 whose max-norm is zero
+ * or not finite gives HOTRG_ENONFINITE.
  */
 hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec,
                           void *stream, hotrg_ctx **out);
@@ -231,15 +235,27 @@ hotrg_status hotrg_create(const double *T0, int D0, int D_cut, hotrg_prec prec,
  * eigensolver (both environments at once): for Dx^2 <= 96 a parallel two-sided
  * Jacobi diagonalisation of the whole matrix (Sec. II.B, Eqs. 5-6), otherwise
  * block subspace iteration with Rayleigh-Ritz steps solved by the same Jacobi
- * method, stopped at a residual of 1e-12 relative to the largest eigenvalue;
- * if that does not converge the step falls back to cuSOLVER's syevdx.
+ * method, stopped at a residual of 1e-12 relative to the largest eigenvalue.
+ * If that bound is not reached within HOTRG_OPT_EIG_MAX_ITERS iterations the
+ * step fails with HOTRG_EEIG (latched; the context keeps the state of the last
+ * completed step).
  */
 hotrg_status hotrg_step(hotrg_ctx *ctx, hotrg_dir dir);
 
-/* ln Z / N after the steps taken so far (synchronises; one small D2H read). */
+/*
+ * ln Z / N after the steps taken so far (Sec. II.A, Eq. 2: Z = Tr T^N over the
+ * N = 2^n sites the n steps have fused): logsum + ln(Tr T_n) / 2^n, with Tr the
+ * periodic trace over both leg pairs of the normalised tensor.  Synchronises
+ * (one small D2H read).  HOTRG_ENONFINITE if the trace is not positive;
+ * HOTRG_ESTATE on a context with more than one instance.
+ */
 hotrg_status hotrg_log_z_per_site(hotrg_ctx *ctx, double *out);
 
-/* f = -(1/beta) ln Z / N (synchronises).  beta must be > 0. */
+/*
+ * Free energy per site f = -(1/beta) ln Z / N (Sec. II.A, Eq. 2, Z = Tr T^N;
+ * J = 1).  beta must be > 0 (HOTRG_EINVAL otherwise).  Synchronises; errors as
+ * for hotrg_log_z_per_site.
+ */
 hotrg_status hotrg_free_energy(hotrg_ctx *ctx, double beta, double *f_out);
 
 /* Diagnostics of step `step` (0-based, < number of steps taken). */
@@ -288,11 +304,25 @@ hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
  *       and replayed afterwards (with the stage profiler on, its events are
  *       part of the graph).  Needs a non-NULL stream (not the legacy default
  *       stream); results are bit-identical either way.
+ *   HOTRG_OPT_EIG_MAX_ITERS  1..1000 (default 80): subspace iterations the
+ *       eigensolver may take per step before the step fails with HOTRG_EEIG.
+ *   HOTRG_OPT_WAIT_CYCLES  >= 1 (default 2e9, about 1 s): bound, in SM clock
+ *       cycles, of every pipeline wait in the tensor-core kernels; a wait that
+ *       runs out makes the kernel record the failure, let its own copies and
+ *       MMAs finish, release its tensor memory and return, and the step reports
+ *       HOTRG_ETIMEOUT.  Process-wide (every context), for launches made after
+ *       the call; segments already captured into CUDA graphs keep the bound
+ *       they were captured with.
+ *   HOTRG_OPT_TEST_STALL  1: testing aid for the timeout path.  The next
+ *       tensor-core GEMM launched in the process (by any context) issues no
+ *       operand copies, so its pipeline waits find a barrier nothing arrives at
+ *       and run out after HOTRG_OPT_WAIT_CYCLES; one-shot.
  * Returns HOTRG_EINVAL for an unknown option or value.
  */
 enum {
   HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1, HOTRG_OPT_GEMM_AUTOTUNE = 2,
-  HOTRG_OPT_GRAPHS = 3
+  HOTRG_OPT_GRAPHS = 3, HOTRG_OPT_EIG_MAX_ITERS = 4, HOTRG_OPT_WAIT_CYCLES = 5,
+  HOTRG_OPT_TEST_STALL = 6
 };
 hotrg_status hotrg_set_option(hotrg_ctx *ctx, int option, int value);
 
@@ -345,35 +375,41 @@ hotrg_status hotrg_profile_read(hotrg_ctx *ctx, hotrg_profile_t *out);
  *   logsum  device pointer to one double, updated in place
  *   stream  cudaStream_t to run on (NULL = legacy default stream)
  * Returns HOTRG_OK, HOTRG_EINVAL, HOTRG_ECUDA, or HOTRG_ENONFINITE when max|T|
- * is zero or not finite (T and *logsum are then left unchanged).  The call
- * synchronises `stream` to read its status.  It allocates nothing: its scratch
- * (1024 partial maxima and a status word, about 8 KiB) is one file-scope
- * device array that every GPU loading the library holds until the process
- * exits.  The first call on each device resolves that array's device address
- * (with the device current), so make it before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.
+ * is zero or not finite (T and *logsum are then left unchanged).  Every call,
+ * the first included, copies its status word to host memory and synchronises
+ * `stream` before it returns.  It allocates nothing: its scratch (1024 partial
+ * maxima and a status word, about 8 KiB) is one file-scope device array that
+ * every GPU loading the library holds until the process exits.  The first call
+ * on each device resolves that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.
  */
 hotrg_status hotrg_rescale_noalloc(double *T, long long count, double weight, double *logsum,
                                    void *stream);
 
 /*
  * Batches (many independent lattice models in one context).  Every instance
- * is its own HOTRG run with its own T0 and D_cut; all instances take the same
- * step directions.  Instances with equal (D0, D_cut) have equal bond
+ * is its own HOTRG run with its own T0 and D_cut -- the step of Sec. II.A
+ * (contraction of two tensors along one bond, fused legs cut by the SVD of the
+ * reshaped pair) applied to each instance's own Z = Tr T^N (Eq. 2); all
+ * instances take the same step directions.  Instances with equal (D0, D_cut) have equal bond
  * dimensions after every step and are grouped: each kernel of a step runs once
  * per group over all its instances, and the eigensolver diagonalises the
  * group's 2G environments as one batch.  Results of an instance do not depend
  * on which other instances share its context.
  *
  * hotrg_batch_create: n instances (1 <= n <= 4096); T0s[i] is a host pointer
- *   to D0s[i]^4 doubles ([x,x',y,y'] row-major, borrowed and copied),
- *   1 <= D0s[i] <= 64 and 1 <= Dcuts[i] <= 64.  prec, stream, ownership and
- *   errors as for hotrg_create (all device memory is allocated here).
- * hotrg_batch_step: one step of every instance (same as hotrg_step).
+ *   to D0s[i]^4 doubles ([x,x',y,y'] row-major, borrowed and copied): the local
+ *   tensor of instance i (Sec. II.A, Eq. 2), 1 <= D0s[i] <= 64 and
+ *   1 <= Dcuts[i] <= 64.  prec, stream, ownership and errors as for
+ *   hotrg_create (all device memory is allocated here).
+ * hotrg_batch_step: one coarse-graining step (Sec. II.A) of every instance,
+ *   same as hotrg_step.
  * hotrg_batch_size: number of instances.
- * hotrg_batch_log_z: ln Z / N of every instance, in creation order, into
- *   out_n[0..n) (host, n doubles; synchronises).
+ * hotrg_batch_log_z: ln Z / N of every instance (Sec. II.A, Eq. 2, as for
+ *   hotrg_log_z_per_site), in creation order, into out_n[0..n) (host, n
+ *   doubles; synchronises).
  * hotrg_batch_step_info / hotrg_batch_get_tensor: hotrg_step_info and
  *   hotrg_get_tensor for instance `inst` (0-based, creation order).
  * On a context with more than one instance, hotrg_log_z_per_site and

@@ -2,7 +2,7 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel to an object file
 under ``_build/`` and linked into ``paper_2602_05900_gb300/libhotrg.so``
-against the shared CUDA runtime and cuSOLVER.  Nothing is installed.
+against the shared CUDA runtime.  Nothing is installed.
 """
 from __future__ import annotations
 
@@ -72,7 +72,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
         if not os.path.isdir(libdir):
             libdir = os.path.join(cuda, "lib")
         cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + ["-o", LIB] + objs + [
-            "-L", libdir, "-lcusolver", "-Xlinker", "-rpath", "-Xlinker", libdir]
+            "-L", libdir, "-Xlinker", "-rpath", "-Xlinker", libdir]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -27,6 +27,10 @@ OPT_EIG_TC_PRODUCTS = 0
 OPT_XS_DIGITS = 1
 OPT_GEMM_AUTOTUNE = 2
 OPT_GRAPHS = 3
+OPT_EIG_MAX_ITERS = 4
+OPT_WAIT_CYCLES = 5
+OPT_TEST_STALL = 6
+WAIT_CYCLES_DEFAULT = 2_000_000_000
 
 
 class StepInfo(ctypes.Structure):

@@ -419,17 +419,52 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
     if (threadIdx.x == 0) atomicExch(flag, 1);
     return;
   }
-  // W = R^-1 diag-scaled: column c of R^-1 by back substitution, one thread per
-  // column (columns are independent; no barriers), W[j + c m] = d_j (R^-1)_jc
-  double *W = Wout.at(z);
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    float *zc = C + c;                              // column c of the (now free) C storage
-    for (int i = c; i >= 0; --i) {
+  // W = diag(d) R^-1.  Z = R^-1 (upper triangular, in the now free C storage)
+  // by panels of kCholPanel rows, the bottom panel first: for the panel's rows
+  // i and every column c >= i, t_ic = [i == c] - sum_{l past the panel, l <= c}
+  // R_il Z_lc (independent dot products, all threads), then each column solves
+  // the panel's small upper triangle R_II z = t (one thread per column).  Two
+  // barriers per panel instead of a dependent chain of length m per column.
+  float *Z = C;
+  float *rinv = d + m;                    // m: 1 / R_ii
+  float *Tp = rinv + m;                   // kCholPanel x m: right-hand sides of a panel
+  for (int i = threadIdx.x; i < m; i += blockDim.x) rinv[i] = 1.0f / R[i * ld + i];
+  __syncthreads();
+  const int last = ((m - 1) / kCholPanel) * kCholPanel;
+  for (int i0 = last; i0 >= 0; i0 -= kCholPanel) {
+    const int w = min(kCholPanel, m - i0), cols = m - i0;
+    for (int e = threadIdx.x; e < w * cols; e += blockDim.x) {
+      const int ii = e / cols, c = i0 + e % cols, i = i0 + ii;
       float acc = (i == c) ? 1.0f : 0.0f;
-      for (int k = i + 1; k <= c; ++k) acc = fmaf(-R[i * ld + k], zc[k * ld], acc);
-      zc[i * ld] = acc / R[i * ld + i];
+      for (int l = i0 + w; l <= c; ++l) acc = fmaf(-R[i * ld + l], Z[l * ld + c], acc);
+      Tp[ii * m + c] = acc;
     }
-    for (int j = 0; j < m; ++j) W[(size_t)c * m + j] = (j <= c) ? (double)zc[j * ld] * (double)d[j] : 0.0;
+    __syncthreads();
+    for (int c = i0 + threadIdx.x; c < m; c += blockDim.x) {
+      float zc[kCholPanel];
+#pragma unroll
+      for (int ii = kCholPanel - 1; ii >= 0; --ii) {
+        const int i = i0 + ii;
+        float v = 0.0f;
+        if (ii < w && i <= c) {
+          v = Tp[ii * m + c];
+#pragma unroll
+          for (int kk = ii + 1; kk < kCholPanel; ++kk)
+            if (kk < w) v = fmaf(-R[i * ld + i0 + kk], zc[kk], v);
+          v *= rinv[i];
+        }
+        zc[ii] = v;
+      }
+#pragma unroll
+      for (int ii = 0; ii < kCholPanel; ++ii)
+        if (ii < w) Z[(i0 + ii) * ld + c] = zc[ii];
+    }
+    __syncthreads();
+  }
+  double *W = Wout.at(z);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int c = e / m, j = e % m;           // W[j + c m]
+    W[e] = (j <= c) ? (double)Z[j * ld + c] * (double)d[j] : 0.0;
   }
 }
 
@@ -937,7 +972,7 @@ size_t jacobi_smem(int m) {
          (size_t)(4 * half) * sizeof(int) + 64;
 }
 size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
-size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + m) * sizeof(float); }
+size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m + kCholPanel * m) * sizeof(float); }
 
 cudaError_t set_attrs() {
   static bool done = false;

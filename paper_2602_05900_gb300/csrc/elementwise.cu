@@ -97,7 +97,7 @@ __global__ void k_scale(double *T, long long count, long long sT, const unsigned
       logsum[inst * sLog] += lc * inv_two_pow_n;
       if (ln_c_out) ln_c_out[inst * sLnc] = lc;
     } else {
-      atomicExch(err, 1);
+      atomicMax(err, 1);
       if (ln_c_out) ln_c_out[inst * sLnc] = NAN;
     }
   }

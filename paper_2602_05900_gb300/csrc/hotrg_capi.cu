@@ -34,11 +34,11 @@
 
 #include "../../include/hotrg.h"
 #include "common.cuh"
-#include "eig.cuh"
 #include "eig_si.cuh"
 #include "tc_exact.cuh"
 #include "tc_gemm.cuh"
 #include "tc_path.cuh"
+#include "tcgen05.cuh"
 #include "xxz.cuh"
 
 using namespace hotrg;
@@ -209,13 +209,11 @@ struct Group {
   long long sT = 0;               // T, Tn, partials, Gram matrices: Dm^4
   long long sU = 0;               // U: Dm^2 (D_cut + 1)
   long long sUp = 0;              // previous isometry per direction: Dm^2 D_cut
-  long long sW = 0;               // library-fallback eigenvalues: Dm^2
   long long sP = 0;               // FP64 P and Q: D_cut Dm^4
   long long sRec = 0, sSpec = 0;  // step records / spectra per instance
   double *T = nullptr, *Tn = nullptr;
   double *AL = nullptr, *BL = nullptr, *AR = nullptr, *BR = nullptr;
   double *GL = nullptr, *GR = nullptr;
-  double *wL = nullptr, *wR = nullptr;
   double *U = nullptr, *P = nullptr, *Q = nullptr;
   // tensor-core modes: FP64 partials and P, Q of the steps with D = 1 (each
   // Dm^2 per instance at stride sC1; the full-size buffers above stay unset)
@@ -252,7 +250,6 @@ struct Group {
 struct hotrg_ctx {
   Profiler prof;
   cudaStream_t stream = nullptr;
-  Eig eig;
   hotrg_prec prec = HOTRG_FP64;
   int nsteps = 0;
   int n_inst = 0;
@@ -262,6 +259,7 @@ struct hotrg_ctx {
   bool eig_tc = true;                       // exact-slice tensor-core products G X
   bool use_graphs = true;                   // replay contraction segments as CUDA graphs
   int xs_digits = 6;                        // digits of the exact-slice contraction mode
+  int eig_max_iters = 80;                   // subspace iterations before HOTRG_EEIG
   int *err = nullptr;
   hotrg_status status = HOTRG_OK;
   std::string msg;
@@ -332,14 +330,12 @@ hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
   g.sT = round_up(t4, 32);
   g.sU = round_up(nmax * (g.D_cut + 1), 32);
   g.sUp = round_up(nmax * g.D_cut, 32);
-  g.sW = round_up(nmax, 32);
   g.sP = round_up((long long)g.D_cut * t4, 32);
   g.sRec = (long long)kMaxSteps * kRecord;
   g.sSpec = round_up((long long)kMaxSteps * (g.D_cut + 1), 32);
   hotrg_status s;
   if ((s = dalloc(c, &g.T, g.sT * G)) || (s = dalloc(c, &g.Tn, g.sT * G)) ||
       (s = dalloc(c, &g.GL, g.sT * G)) || (s = dalloc(c, &g.GR, g.sT * G)) ||
-      (s = dalloc(c, &g.wL, g.sW * G)) || (s = dalloc(c, &g.wR, g.sW * G)) ||
       (s = dalloc(c, &g.U, g.sU * G)) || (s = dalloc(c, &g.scal, (long long)kScal * G)) ||
       (s = dalloc(c, &g.records, g.sRec * G)) || (s = dalloc(c, &g.spectra, g.sSpec * G)) ||
       (s = dalloc(c, &g.Uprev[0], g.sUp * G)) || (s = dalloc(c, &g.Uprev[1], g.sUp * G)))
@@ -439,7 +435,6 @@ hotrg_status create_ctx(int n, const double *const *T0s, const int *D0s, const i
     si_doubles = std::max(si_doubles, si_workspace_doubles(2 * g.G, nsi, kSiMaxBlock));
   }
   if ((s = dalloc(c, &c->si_work, (size_t)si_doubles))) return bail(s);
-  if (int r = c->eig.init(c->stream)) return bail(r == 2 ? HOTRG_ENOMEM : HOTRG_ECUDA);
   if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) return bail(HOTRG_ECUDA);
   for (auto &gp : c->groups) {
     Group &g = *gp;
@@ -666,7 +661,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
         sb.kw = g.kprev[di];
       }
       SiResult r{};
-      CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, 80, st, &r, &nl));
+      CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, c->eig_max_iters, st, &r, &nl));
       eig_path = 2;
       eig_iters = r.iterations;
       g.iters_prev[di] = r.converged ? r.iterations : 0;
@@ -674,29 +669,14 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       ok = r.converged;
     }
     pf.launched(HOTRG_ST_EIG, (int)nl);
-    if (ok) {
+    if (!ok)
+      return fail(c, HOTRG_EEIG,
+                  "eigensolver did not reach its residual bound in " + std::to_string(c->eig_max_iters) +
+                      " subspace iterations (residual " + std::to_string(eig_res) + ")");
+    {
       const SiOut o = si_outputs(c->si_work, 2 * G, n, sb.m);
       SelectArgs a{n, Dn, k, 1, o.theta, o.X, g.scal + 2, kScal, g.U, g.sU,
                    rec, g.sRec, spec, g.sSpec, G};
-      CK_CUDA(c, select_isometry(a, st));
-    } else {
-      // library fallback, one environment at a time (the own solver leaves
-      // G_L and G_R untouched); vectors overwrite the leading columns of G
-      eig_path = 3;
-      for (int j = 0; j < G; ++j) {
-        if (int r = c->eig.top(g.GL + j * g.sT, n, k, g.wL + j * g.sW, 0))
-          return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (left) failed");
-        if (int r = c->eig.top(g.GR + j * g.sT, n, k, g.wR + j * g.sW, 1))
-          return fail(c, r == 2 ? HOTRG_ENOMEM : HOTRG_EEIG, "eigensolver (right) failed");
-        int hinfo[2] = {0, 0};
-        CK_CUDA(c, cudaMemcpyAsync(hinfo, c->eig.d_info(), sizeof(hinfo), cudaMemcpyDeviceToHost, st));
-        CK_CUDA(c, cudaStreamSynchronize(st));
-        if (hinfo[0] != 0 || hinfo[1] != 0)
-          return fail(c, HOTRG_EEIG, "eigensolver info = " + std::to_string(hinfo[0]) + ", " +
-                                         std::to_string(hinfo[1]));
-      }
-      SelectArgs a{n, Dn, k, 0, pset_pairs(g.wL, g.wR, g.sW), pset_pairs(g.GL, g.GR, g.sT),
-                   g.scal + 2, kScal, g.U, g.sU, rec, g.sRec, spec, g.sSpec, G};
       CK_CUDA(c, select_isometry(a, st));
     }
     pf.launched(HOTRG_ST_EIG, 1);
@@ -965,6 +945,18 @@ hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
     case HOTRG_OPT_GRAPHS:
       if (value != 0 && value != 1) return HOTRG_EINVAL;
       c->use_graphs = value != 0;
+      return HOTRG_OK;
+    case HOTRG_OPT_EIG_MAX_ITERS:
+      if (value < 1 || value > 1000) return HOTRG_EINVAL;
+      c->eig_max_iters = value;
+      return HOTRG_OK;
+    case HOTRG_OPT_WAIT_CYCLES:
+      if (value < 1) return HOTRG_EINVAL;
+      tc::set_wait_limit(value);
+      return HOTRG_OK;
+    case HOTRG_OPT_TEST_STALL:
+      if (value != 1) return HOTRG_EINVAL;
+      tc::arm_stall();
       return HOTRG_OK;
   }
   return HOTRG_EINVAL;

@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(256) k_xs_split_staged(PSet src, int R, int K,
 template <int S, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_xs_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-              int M, int N, int K, int kb_per_part, int ntn, XsOut o, int *err_flag) {
+              int M, int N, int K, int kb_per_part, int ntn, XsOut o, int *err_flag,
+              long long wait, int stall) {
   using C = XsCfg<S, BN>;
   constexpr XsTable<S> T{};
   constexpr int STAGES = C::STAGES;
@@ -246,10 +247,10 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
     int i = 0;
-    for (; i < nk; ++i) {
+    for (; i < (stall ? 0 : nk); ++i) {    // a stalled launch issues nothing
       const int s = i % STAGES;
       const uint32_t ph = (i / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
+      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, wait)) {
         atomicExch(&s_fail, 1);
         break;
       }
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(128, 1)
     for (; i < nk; ++i) {
       const int s = i % STAGES;
       const uint32_t ph = (i / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
+      if (!mbar_wait(smem_u32(&full_bar[s]), ph, wait)) {
         atomicExch(&s_fail, 1);
         break;
       }
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(128, 1)
   __syncwarp();
 
   // ---- epilogue: thread (warp w, lane l) owns accumulator row 32 w + l
-  const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0);
+  const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0, wait);
   fence_after();
   if (!acc_ok) atomicExch(&s_fail, 1);
   const bool ok = acc_ok && nk > 0 && (*(volatile int *)&s_fail == 0);
@@ -345,9 +346,11 @@ __global__ void __launch_bounds__(128, 1)
   fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (s_fail) atomicExch(err_flag, 2);
+    if (s_fail) atomicMax(err_flag, 2);   // a timeout outranks the non-finite flag (1) it may cause
     for (int i = s_consumed; i < s_issued; ++i)
       (void)mbar_wait(smem_u32(&full_bar[i % STAGES]), (i / STAGES) & 1);
+    // the MMAs (acc_bar tracks all of them) finish before the dealloc
+    (void)mbar_wait(smem_u32(&acc_bar), 0);
   }
   __syncthreads();
   if (warp == 1) {
@@ -398,7 +401,9 @@ cudaError_t launch_xs(const XsOperand &A, const XsOperand &B, int M, int N, int 
   const int batch = A.batch < 1 ? 1 : A.batch;
   dim3 grid(ntn * ksplit, (M + C::BM - 1) / C::BM, batch);
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
-  k_xs_gemm<S, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, kbp, ntn, o, err);
+  const int stall = take_stall() ? 1 : 0;
+  k_xs_gemm<S, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, kbp, ntn, o, err, wait_limit(),
+                                              stall);
   return cudaGetLastError();
 }
 

@@ -8,9 +8,9 @@
 //                     stage to release it back to the producer;
 //   warps 0-3         epilogue: tcgen05.ld of the thread's accumulator row,
 //                     stores through the output index maps.
-// Every mbarrier wait is bounded (about a second); on timeout the kernel sets
-// *err_flag, waits (bounded) for its own TMA copies in flight, frees its tensor
-// memory and returns.
+// Every pipeline wait is bounded (wait_limit(), about a second by default); on
+// timeout the kernel sets *err_flag, waits (with the default bound) for its own
+// TMA copies and MMAs still in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -130,7 +130,8 @@ struct Cfg {
 template <int MODE, int BN>
 __global__ void __launch_bounds__(384, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-              int M, int N, int K, int batch, TcEpilogue epi, int *err_flag) {
+              int M, int N, int K, int batch, TcEpilogue epi, int *err_flag, long long wait,
+              int stall) {
   using C = Cfg<MODE, BN>;
   using Tr = typename C::Tr;
   constexpr int STAGES = C::STAGES;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(384, 1)
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_fail, s_issued, s_consumed;
 
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(384, 1)
       mbar_init(smem_u32(&acc_full[b]), 1);
       mbar_init(smem_u32(&acc_empty[b]), C::EPI_WARPS);   // one arrival per epilogue warp
     }
+    mbar_init(smem_u32(&drain_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
     s_issued = 0;
@@ -191,14 +193,14 @@ __global__ void __launch_bounds__(384, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
     int g = 0;
-    bool ok = true;
+    bool ok = !stall;     // a stalled launch issues nothing: its consumers' waits run out
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int n0, m0, z;
       tile_coords(t, n0, m0, z);
       for (int kb = 0; kb < nkb; ++kb, ++g) {
         const int s = g % STAGES;
         const uint32_t ph = (g / STAGES) & 1;
-        if (failed() || !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
+        if (failed() || !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, wait)) {
           atomicExch(&s_fail, 1);
           ok = false;
           break;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(384, 1)
     bool ok = true;
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
       const int buf = i & 1;
-      if (failed() || !mbar_wait(smem_u32(&acc_empty[buf]), ((i >> 1) & 1) ^ 1)) {
+      if (failed() || !mbar_wait(smem_u32(&acc_empty[buf]), ((i >> 1) & 1) ^ 1, wait)) {
         atomicExch(&s_fail, 1);
         break;
       }
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(384, 1)
       for (int kb = 0; kb < nkb; ++kb, ++g) {
         const int s = g % STAGES;
         const uint32_t ph = (g / STAGES) & 1;
-        if (failed() || !mbar_wait(smem_u32(&full_bar[s]), ph)) {
+        if (failed() || !mbar_wait(smem_u32(&full_bar[s]), ph, wait)) {
           atomicExch(&s_fail, 1);
           ok = false;
           break;
@@ -249,6 +251,8 @@ __global__ void __launch_bounds__(384, 1)
       }
       if (ok) mma_commit(smem_u32(&acc_full[buf]));
     }
+    // tracks every MMA this thread issued: the teardown waits for it
+    mma_commit(smem_u32(&drain_bar));
   } else if (warp >= 4) {
     // ---- epilogue warps: thread (warp w, lane l) owns accumulator row 32 (w mod 4) + l
     const int ew = warp - 4;
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(384, 1)
     int i = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int buf = i & 1;
-      if (failed() || !mbar_wait(smem_u32(&acc_full[buf]), (i >> 1) & 1)) {
+      if (failed() || !mbar_wait(smem_u32(&acc_full[buf]), (i >> 1) & 1, wait)) {
         atomicExch(&s_fail, 1);
         break;
       }
@@ -308,10 +312,12 @@ __global__ void __launch_bounds__(384, 1)
   fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (s_fail) atomicExch(err_flag, 2);
+    if (s_fail) atomicMax(err_flag, 2);   // a timeout outranks the non-finite flag (1) it may cause
     // TMA copies issued but never consumed (only after a timeout): let them land
     for (int g = s_consumed; g < s_issued; ++g)
       (void)mbar_wait(smem_u32(&full_bar[g % STAGES]), (g / STAGES) & 1);
+    // MMAs still running (only after a timeout) must finish before the dealloc
+    (void)mbar_wait(smem_u32(&drain_bar), 0);
   }
   __syncthreads();
   if (warp == 2) {
@@ -347,6 +353,7 @@ bool make_map(CUtensorMap *m, TcMode mode, const TcOperand &op, int box_rows) {
 template <int MODE, int BN>
 cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int batch,
                    const TcEpilogue &epi, int *err, cudaStream_t s) {
+  const int stall = take_stall() ? 1 : 0;
   using C = Cfg<MODE, BN>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -364,7 +371,8 @@ cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, i
   }
   const long long tiles = (long long)((N + BN - 1) / BN) * ((M + C::BM - 1) / C::BM) * batch;
   const int grid = (int)(tiles < nsm ? tiles : nsm);
-  k_tc_gemm<MODE, BN><<<grid, 384, C::SMEM, s>>>(ta, tb, M, N, K, batch, epi, err);
+  k_tc_gemm<MODE, BN><<<grid, 384, C::SMEM, s>>>(ta, tb, M, N, K, batch, epi, err, wait_limit(),
+                                                  stall);
   return cudaGetLastError();
 }
 
@@ -453,6 +461,16 @@ cudaError_t dispatch_bn(const TcOperand &A, const TcOperand &B, int M, int N, in
 }  // namespace
 
 namespace tc {
+
+namespace {
+std::atomic<long long> g_wait_limit{kWaitCycles};
+std::atomic<bool> g_stall{false};
+}  // namespace
+
+void set_wait_limit(long long cycles) { g_wait_limit.store(cycles > 0 ? cycles : kWaitCycles); }
+long long wait_limit() { return g_wait_limit.load(); }
+void arm_stall() { g_stall.store(true); }
+bool take_stall() { return g_stall.exchange(false); }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -12,7 +12,12 @@
 namespace hotrg {
 namespace tc {
 
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at the GB300 boost clock
+// Default bound of a pipeline wait (~1 s at the GB300 boost clock).  The bound
+// a kernel uses is a launch argument (wait_limit() on the host); the waits of
+// a kernel's teardown -- for its own copies and MMAs still in flight after a
+// pipeline wait gave up -- always use this default, so that nothing the kernel
+// started can still write to its shared or tensor memory once it returns.
+constexpr long long kWaitCycles = 2000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -39,12 +44,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false after about a second without the phase completing.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait: false once `limit` cycles pass without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -128,6 +133,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 // cuTensorMapEncodeTiled from the driver (resolved once; null if unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
+
+// Process-wide bound (cycles) of the pipeline waits of the tensor-core kernels
+// launched from now on (kernels already captured into CUDA graphs keep theirs).
+void set_wait_limit(long long cycles);
+long long wait_limit();
+// Test hook: the next tensor-core GEMM launched in the process issues no
+// operand copies, so its pipeline waits run out (a barrier nothing arrives
+// at) and it reports a timeout through its error flag.  One-shot.
+void arm_stall();
+bool take_stall();
 
 }  // namespace tc
 }  // namespace hotrg

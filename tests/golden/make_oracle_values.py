@@ -5,7 +5,9 @@ library is never imported.  Each classical entry holds ln Z / N after the
 workload's step count, the free energy per site, and the per-step ln c_n,
 discarded weights, side and normalised spectrum head of the chosen
 environment; each quantum-chain entry (D_cut <= 32) holds ln Z / N_cells and
-the free energy per site of the whole schedule.
+the free energy per site of the whole schedule; ``sweep_subset16`` holds
+ln Z / N of each instance of the seeded 16-instance subset of the batched
+sweep.
 
     python tests/golden/make_oracle_values.py [name ...]
 
@@ -20,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle import heisenberg, hotrg  # noqa: E402
-from workloads import CONFIGS, QUANTUM_CONFIGS  # noqa: E402
+from workloads import CONFIGS, QUANTUM_CONFIGS, sweep_subset  # noqa: E402
 
 OUT = os.path.join(HERE, "oracle_values.json")
 
@@ -61,13 +63,32 @@ def compute_quantum(q):
     }
 
 
+def compute_sweep_subset():
+    """ln Z / N of the 16-instance subset of the batched sweep (4 per cut group,
+    25 steps each), with each run's smallest relative gap at the cut."""
+    t0 = time.time()
+    rows = []
+    for m in sweep_subset():
+        r = hotrg.run(hotrg.ising_initial_tensor(m.beta, m.h), m.D_cut, m.steps)
+        gaps = [s.cut_gap for s in r.steps if s.cut_gap != float("inf")]
+        rows.append({"name": m.name, "beta": m.beta, "h": m.h, "D_cut": m.D_cut, "steps": m.steps,
+                     "ln_z_per_site": r.ln_z_per_site, "min_cut_gap": min(gaps) if gaps else None})
+        print(f"  {m.name} D_cut={m.D_cut} beta={m.beta:.6f}: ln Z/N = {r.ln_z_per_site:.16f}", flush=True)
+    return {"instances": rows, "first": "x", "oracle_seconds": time.time() - t0,
+            "ln_z_per_site": rows[0]["ln_z_per_site"]}
+
+
 def main(names):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
-    every = list(CONFIGS) + [n for n in QUANTUM_CONFIGS if QUANTUM_CONFIGS[n].D_cut <= 32]
+    every = (list(CONFIGS) + [n for n in QUANTUM_CONFIGS if QUANTUM_CONFIGS[n].D_cut <= 32]
+             + ["sweep_subset16"])
     todo = names or [n for n in every if n not in data]
     for name in todo:
         print(f"oracle: {name} ...", flush=True)
-        data[name] = compute(CONFIGS[name]) if name in CONFIGS else compute_quantum(QUANTUM_CONFIGS[name])
+        if name == "sweep_subset16":
+            data[name] = compute_sweep_subset()
+        else:
+            data[name] = compute(CONFIGS[name]) if name in CONFIGS else compute_quantum(QUANTUM_CONFIGS[name])
         print(f"  ln Z/N = {data[name]['ln_z_per_site']:.16f} ({data[name]['oracle_seconds']:.0f} s)", flush=True)
         json.dump(data, open(OUT, "w"), indent=1)
 

@@ -88,3 +88,25 @@ def test_transient_steps_schedule():
     assert bench.transient_steps(2, 40) == 6
     assert bench.transient_steps(2, 4) == 2
     assert bench.transient_steps(3, 9) == 2
+
+
+def test_clock_sampler_names_the_visible_gpu(monkeypatch):
+    """nvidia-smi numbers GPUs physically: without a device UUID from torch the
+    sampler must use the local-th entry of CUDA_VISIBLE_DEVICES, not the rank."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a visible GPU names itself by UUID")
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,GPU-1234")
+    assert bench.gpu_selector(0) == "5"
+    assert bench.gpu_selector(1) == "GPU-1234"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.gpu_selector(0) == "0"
+
+
+def test_clock_summary_reports_cycles_per_step():
+    s = bench.ClockSampler(0)
+    s.lines = ["2070, 2070, 900, Not Active, Not Active, Not Active, Active",
+               "2060, 2070, 910, Not Active, Not Active, Not Active, Not Active"]
+    out = s.summary(ms_per_step=2.0)
+    assert out["sm_mhz"] == 2065.0 and out["reasons"] == ["sw_power_cap"]
+    assert out["mcycles_per_step"] == round(2.0 * 2065.0 / 1e3, 4)

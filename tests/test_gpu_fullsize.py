@@ -138,3 +138,69 @@ def test_sampled_full_size_step(pkg, name, prec):
     scale = c                                           # max |T'| before the rescale
     tol_t = 1e-12 if prec == "fp64" else 2e-3
     assert np.abs(got - ref_vals).max() < tol_t * scale
+
+
+def test_fp64_potts3_d64_vs_stored_oracle(pkg):
+    """The plain FP64 GPU path on the q = 3 Potts configuration (D_cut = 64, 30
+    steps).  S3 symmetry puts exact multiplets at some cuts: where the stored
+    run's cut falls inside one, the truncated tensor depends on the rotation the
+    eigensolver returns and f agrees only at the truncation-error level."""
+    cfg, g = CONFIGS["potts3_d64"], golden("potts3_d64")
+    gaps = [s["cut_gap"] for s in g["per_step"] if s["cut_gap"] is not None]
+    degenerate = min(gaps) < 1e-9
+    with pkg.Hotrg(initial(pkg, cfg), cfg.D_cut, "fp64") as h:
+        h.run(cfg.steps)
+        lz = h.ln_z_per_site()
+        assert all(h.step_info(i).eig_path in (0, 1, 2) for i in range(cfg.steps))
+    err = abs(lz / g["ln_z_per_site"] - 1)
+    print(f"potts3_d64 fp64: relative ln Z/N error vs FP64 oracle = {err:.3e} (degenerate cut: {degenerate})")
+    assert err < (1e-9 if degenerate else 1e-12)
+
+
+def sweep_rows():
+    data = golden("sweep_subset16")
+    from workloads import sweep_subset
+    models = sweep_subset()
+    rows = data["instances"]
+    assert [r["name"] for r in rows] == [m.name for m in models]
+    return models, rows
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32", 5e-4)])
+def test_batched_sweep_subset_vs_stored_oracle(pkg, prec, tol):
+    """Sixteen instances of the seeded beta sweep (four per cut group, D_cut 16,
+    24, 32, 40, 25 steps) in one batched context against the stored oracle
+    values: every cut group runs at its full size in the same steps.  Instances
+    whose cut falls inside a degenerate multiplet are held to 1e-9 in FP64."""
+    models, rows = sweep_rows()
+    T0s = [pkg.ising_tensor(m.beta, m.h) for m in models]
+    with pkg.HotrgBatch(T0s, [m.D_cut for m in models], prec) as bt:
+        bt.run(models[0].steps)
+        lz = bt.ln_z_per_site()
+    worst = 0.0
+    for i, r in enumerate(rows):
+        err = abs(lz[i] / r["ln_z_per_site"] - 1)
+        worst = max(worst, err)
+        degenerate = r["min_cut_gap"] is not None and r["min_cut_gap"] < 1e-9
+        t = max(tol, 1e-9) if degenerate else tol
+        assert err < t, (r["name"], r["D_cut"], lz[i], r["ln_z_per_site"], err)
+    print(f"sweep subset {prec}: worst relative ln Z/N error vs FP64 oracle = {worst:.3e}")
+
+
+def test_batched_sweep_subset_matches_single_contexts(pkg):
+    """One instance per cut group of the sweep subset, batched (TF32) against
+    the same instance in a context of its own: same kernels and operand
+    rounding, so they agree far below the TF32 error."""
+    models, _ = sweep_rows()
+    T0s = [pkg.ising_tensor(m.beta, m.h) for m in models]
+    with pkg.HotrgBatch(T0s, [m.D_cut for m in models], "tf32") as bt:
+        bt.run(models[0].steps)
+        lz = bt.ln_z_per_site()
+    picked = {}
+    for i, m in enumerate(models):
+        picked.setdefault(m.D_cut, i)
+    for D, i in sorted(picked.items()):
+        with pkg.Hotrg(T0s[i], D, "tf32") as one:
+            one.run(models[i].steps)
+            single = one.ln_z_per_site()
+        assert abs(lz[i] / single - 1) < 1e-9, (D, lz[i], single)

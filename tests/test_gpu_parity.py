@@ -5,7 +5,8 @@ signs and degenerate rotations free): ln Z / N, the normalised spectra of the
 chosen environment at steps whose cut is not degenerate, the discarded weights
 and the step bookkeeping.  FP64 path: <= 1e-12 relative.  Mixed precision:
 the error against the oracle is measured and bounded by the tolerances below
-(derived in the design doc from the operand rounding of each mode).
+(each mode's operand rounding -- TF32 keeps 10 mantissa bits, a two-term BF16
+split about 16 -- damped by the 1/2^n weights of the later steps).
 """
 import math
 
@@ -189,3 +190,49 @@ def test_graph_replay_matches_eager(pkg, prec):
             out[graphs] = (h.ln_z_per_site(), h.tensor())
     assert out[1][0] == out[0][0]
     assert np.array_equal(out[1][1], out[0][1])
+
+
+def test_eigensolver_iteration_cap_gives_eeig(pkg):
+    """A solve that cannot reach its residual bound within the iteration cap
+    fails the step with HOTRG_EEIG (no library fallback); the error is latched
+    and a fresh context is unaffected."""
+    from paper_2602_05900_gb300.capi import HOTRG_EEIG, OPT_EIG_MAX_ITERS
+    T0 = pkg.ising_tensor(0.44)
+    with pkg.Hotrg(T0, 12, "fp64") as h:
+        h.set_option(OPT_EIG_MAX_ITERS, 1)
+        with pytest.raises(pkg.HotrgError) as e:
+            h.run(8)                     # step 4 (Dx = 16 > D_cut) needs the subspace iteration
+        assert e.value.status == HOTRG_EEIG
+        with pytest.raises(pkg.HotrgError) as e2:
+            h.step("x")                  # latched
+        assert e2.value.status == HOTRG_EEIG
+    r = ref.run(ref.ising_initial_tensor(0.44), 12, 8)
+    with run_gpu(pkg, T0, 12, 8) as h:
+        assert abs(h.ln_z_per_site() / r.ln_z_per_site - 1) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16xs"])
+def test_bounded_wait_timeout_is_reported(pkg, prec):
+    """The timeout path of the tensor-core kernels (tcgen05 GEMM, exact-slice
+    GEMM): a launch whose producer issues nothing leaves its consumers waiting
+    on a barrier nothing arrives at; with a short wait bound the kernel gives
+    up, records the failure, releases its tensor memory and returns, and the
+    step reports HOTRG_ETIMEOUT.  The device stays usable: a new context with
+    the default bound reproduces the oracle."""
+    from paper_2602_05900_gb300.capi import (HOTRG_ETIMEOUT, OPT_TEST_STALL, OPT_WAIT_CYCLES,
+                                             WAIT_CYCLES_DEFAULT)
+    T0 = pkg.ising_tensor(0.44, 0.01)
+    try:
+        with pkg.Hotrg(T0, 8, prec) as h:
+            h.run(2)                                  # D = 4: the contractions are tensor-core GEMMs
+            h.set_option(OPT_WAIT_CYCLES, 200_000)    # ~0.1 ms
+            h.set_option(OPT_TEST_STALL, 1)
+            with pytest.raises(pkg.HotrgError) as e:
+                h.step("x")
+            assert e.value.status == HOTRG_ETIMEOUT
+    finally:
+        with pkg.Hotrg(T0, 8, prec) as h2:
+            h2.set_option(OPT_WAIT_CYCLES, WAIT_CYCLES_DEFAULT)
+    r = ref.run(ref.ising_initial_tensor(0.44, 0.01), 8, 8)
+    with run_gpu(pkg, T0, 8, 8, prec) as h:
+        assert abs(h.ln_z_per_site() / r.ln_z_per_site - 1) < MIXED_TOL[prec]

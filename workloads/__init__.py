@@ -92,6 +92,19 @@ def sweep256(seed: int = SEED, n: int = 256, cuts=(16, 24, 32, 40), steps: int =
             for i, (b, d) in enumerate(zip(betas, dcuts))]
 
 
+def sweep_subset(per_group: int = 4, seed: int = SEED):
+    """The first `per_group` instances of every cut group of ``sweep256`` (in
+    creation order): a seeded subset of the batched sweep small enough for the
+    oracle, with all four cut groups."""
+    seen = {}
+    out = []
+    for m in sweep256(seed):
+        if seen.get(m.D_cut, 0) < per_group:
+            seen[m.D_cut] = seen.get(m.D_cut, 0) + 1
+            out.append(m)
+    return out
+
+
 def random_tensor(D0: int, seed: int = SEED, Dy: int | None = None) -> np.ndarray:
     """I.i.d. U[0,1) tensor T[x,x',y,y'] of shape (D0, D0, Dy, Dy) (stress input)."""
     rng = np.random.default_rng(seed)
