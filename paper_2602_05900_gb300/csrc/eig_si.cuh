@@ -34,6 +34,7 @@ struct SiBatch {
   bool has_trace;
   double shift_rel;      // initial shift / Tr G
   int first_check;       // expected convergence iteration (first Rayleigh-Ritz step of small batches)
+  double floor_tol;      // residual accepted once it stops decreasing (0: the FP64 default, 1e-10)
 };
 
 // Where a solve leaves its results inside the workspace: Ritz vectors of

@@ -649,6 +649,17 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       sb.trace = PSet{g.scal + 2, g.scal + 3, kScal};
       sb.has_trace = true;
       sb.shift_rel = 0x1.0p-40;
+      // Environments built from reduced-precision products are accurate to
+      // about the operands' unit roundoff u (TF32 2^-11, two-term BF16 ~2^-17,
+      // three-term ~2^-24): eigenvalues below that level relative to the
+      // largest are noise, with eigenvectors undetermined beyond it, so a
+      // residual that stalls there is accepted (20 u; FP64-grade G: 1e-10).
+      switch (c->prec) {
+        case HOTRG_TF32: sb.floor_tol = 20.0 * 0x1.0p-11; break;
+        case HOTRG_BF16X3: sb.floor_tol = 20.0 * 0x1.0p-17; break;
+        case HOTRG_BF16X6: sb.floor_tol = 20.0 * 0x1.0p-24; break;
+        default: sb.floor_tol = 0.0; break;
+      }
       // the solve of the last step in this direction took iters_prev
       // iterations; a Rayleigh-Ritz step costs several iterations, so the
       // first one is scheduled just before that count
