@@ -47,6 +47,7 @@ constexpr int kCholPanel = 8;      // columns per panel of the blocked FP32 Chol
 constexpr double kXsSmallWork = 32.0 * 1024 * 1024;   // FP64 FMAs of one n x m x m product batch
 constexpr int kSiSmallBatch = 8;      // problems up to which the solve is latency bound
 constexpr double kSiFloorTol = 1e-10;  // residuals accepted once they stop decreasing
+constexpr int kSiSlowIters = 16;       // iterations after which a residual below the floor is accepted
 constexpr float kChol32Retry = 0x1.0p-12f;   // diagonal shift of a retried FP32 CholeskyQR pass
 
 
@@ -1438,7 +1439,11 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       // vectors are not determined beyond that noise).
       const double floor_tol = b.floor_tol > 0.0 ? b.floor_tol : kSiFloorTol;
       const bool stalled = worst <= floor_tol && res->rr >= 2 && worst > 0.5 * prev_worst;
-      if (worst <= tol || stalled) {
+      // In a flat tail of noise-level eigenvalues (reduced-precision G) the
+      // wanted pairs converge at a rate near 1: after kSiSlowIters iterations
+      // a residual below the accuracy floor of G is accepted.
+      const bool slow = b.floor_tol > 0.0 && worst <= floor_tol && it >= kSiSlowIters;
+      if (worst <= tol || stalled || slow) {
         res->converged = true;
         break;
       }
