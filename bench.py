@@ -335,10 +335,14 @@ def eig_block(prof, steps, D, measured, info):
     ms = prof["ms"]["eig"] / max(1, steps)
     dense = 2 * (4.0 / 3.0) * n ** 3
     fp64 = measured.get("fp64_tflops") or 1.0
-    iters = [i.eig_iters for i in info if i.eig_path == 2]
+    sub = [i for i in info if i.eig_path == 2]
+    mean = lambda xs: round(statistics.mean(xs), 2) if xs else None
     return {"ms_per_step": round(ms, 4), "share_of_step": None,
             "n": n, "pairs_per_side": D + 1,
-            "subspace_iterations_per_step": round(statistics.mean(iters), 2) if iters else None,
+            "subspace_iterations_per_step": mean([i.eig_iters for i in sub]),
+            "rayleigh_ritz_per_step": mean([i.eig_rr for i in sub]),
+            "jacobi_sweeps_fp32_per_rr": mean([i.eig_sweeps32 for i in sub]),
+            "jacobi_sweeps_fp64_per_rr": mean([i.eig_sweeps for i in sub]),
             "dense_fp64_tridiagonalisation_flops": dense,
             "dense_fp64_lower_bound_ms": round(dense / (fp64 * 1e12) * 1e3, 4),
             "fp64_peak_tflops": fp64,

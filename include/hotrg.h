@@ -101,6 +101,9 @@ typedef struct {
                        2 subspace iteration                                         */
   int eig_iters;    /* subspace iterations (path 2)                                */
   double eig_residual; /* max_i<=D' ||G u_i - lambda_i u_i|| / lambda_1 (path 2)    */
+  int eig_rr;       /* Rayleigh-Ritz steps of the subspace iteration (path 2)      */
+  int eig_sweeps;   /* most FP64 Jacobi sweeps of one Rayleigh-Ritz step (path 2)  */
+  int eig_sweeps32; /* most FP32 Jacobi sweeps of one Rayleigh-Ritz step (path 2)  */
 } hotrg_step_info_t;
 
 /*

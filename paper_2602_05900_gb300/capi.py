@@ -40,7 +40,8 @@ class StepInfo(ctypes.Structure):
                 ("eps_L", ctypes.c_double), ("eps_R", ctypes.c_double),
                 ("cut_gap", ctypes.c_double), ("trace_G", ctypes.c_double),
                 ("eig_path", ctypes.c_int), ("eig_iters", ctypes.c_int),
-                ("eig_residual", ctypes.c_double)]
+                ("eig_residual", ctypes.c_double), ("eig_rr", ctypes.c_int),
+                ("eig_sweeps", ctypes.c_int), ("eig_sweeps32", ctypes.c_int)]
 
 
 STAGES = ["prep", "env", "gram", "eig", "proj_p", "proj_q", "proj_t", "rescale"]

@@ -590,7 +590,7 @@ __device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &
 }
 
 __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout, PSet theta, int *flag,
-                                                   int *sweeps) {
+                                                   int *sweeps, int floor_exp) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int z = blockIdx.z;
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
     double v = 0.0;
     for (int i = threadIdx.x; i < m; i += 32) v = fmax(v, fabs(Cin.at(z)[(size_t)i * m + i]));
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) s_floor = v * 0x1.0p-56;
+    if (threadIdx.x == 0) s_floor = ldexp(v, -floor_exp);
   }
   __syncthreads();
   // the round-0 inputs are read locally; remote writes only target buffer 1
@@ -813,9 +813,12 @@ size_t j32_smem(int m) {
 // round-robin pair order (every pair meets once per sweep).  Vout (FP64,
 // column-major) receives the accumulated rotation V (columns in the order of
 // the final diagonal, unsorted).  A pair is rotated while |h_pq| exceeds both
-// 2^-26 of the largest diagonal entry (a quarter ulp of the matrix norm in
-// FP32) and 1e-7 of sqrt|h_pp h_qq|; the sweeps stop when none was rotated.
-__global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m, PSet Vout) {
+// 2^-22 of the largest diagonal entry and 1e-6 of sqrt|h_pp h_qq|: above the
+// rounding noise each FP32 rotation leaves (about 2^-24 of the matrix norm),
+// which would otherwise keep being rotated; the FP64 stage removes what is
+// left.  The sweeps stop when none was rotated; the count goes to *sweeps
+// (maximum over problems).
+__global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m, PSet Vout, int *sweeps) {
   extern __shared__ float jsh[];
   const int ld = m + 1, half = m / 2;
   float *A = jsh;
@@ -843,8 +846,9 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
-  const float floor_abs = 0x1.0p-26f;      // the scaled largest diagonal entry lies in [1, 2)
-  for (int sweep = 0; sweep < kJ32MaxSweeps; ++sweep) {
+  const float floor_abs = 0x1.0p-22f;      // the scaled largest diagonal entry lies in [1, 2)
+  int sweep = 0;
+  for (; sweep < kJ32MaxSweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int r = 0; r < m - 1; ++r) {
@@ -853,7 +857,7 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
         const int p = min(u, v), q = max(u, v);
         const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
         float c = 1.0f, sv = 0.0f;
-        if (fabsf(apq) > floor_abs && apq * apq > 1e-14f * fabsf(app * aqq)) {
+        if (fabsf(apq) > floor_abs && apq * apq > 1e-12f * fabsf(app * aqq)) {
           const float tau = (aqq - app) / (2.0f * apq);
           const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
           c = rsqrtf(fmaf(t, t, 1.0f));
@@ -897,6 +901,7 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
     __syncthreads();
     if (!rot) break;
   }
+  if (threadIdx.x == 0) atomicMax(sweeps, sweep + 1);
   double *out = Vout.at(z);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int c = e / m, j = e % m;            // out[j + c m] = V[j][c]
@@ -1140,7 +1145,7 @@ int grid_1d(long long count, int P) {
 }
 
 cudaError_t launch_jacobi(PSet C, int m, PSet W, PSet theta, int *flag, int *sweeps, int P,
-                          cudaStream_t s) {
+                          cudaStream_t s, int floor_exp = 56) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(kCluster, 1, P);
   cfg.blockDim = dim3(512, 1, 1);
@@ -1153,7 +1158,7 @@ cudaError_t launch_jacobi(PSet C, int m, PSet W, PSet theta, int *flag, int *swe
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_si_jacobi, C, m, W, theta, flag, sweeps);
+  return cudaLaunchKernelEx(&cfg, k_si_jacobi, C, m, W, theta, flag, sweeps, floor_exp);
 }
 
 }  // namespace
@@ -1324,7 +1329,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     auto slot = [&](int i) { return PSet{B.Cp.b0 + i * L.mm, B.Cp.b1 + i * L.mm, B.Cp.stride}; };
     const PSet V1 = slot(0), V2 = slot(1), T1 = slot(2);
     const dim3 gmm((m + 7) / 8, (m + 7) / 8, P);
-    k_rr_jacobi32<<<gz, kJ32Threads, j32_smem(m), s>>>(B.C, m, V1);
+    k_rr_jacobi32<<<gz, kJ32Threads, j32_smem(m), s>>>(B.C, m, V1, B.flag + 3);
     k_rr_mm<<<gmm, 256, 0, s>>>(V1, 1, V1, 1.0, 0.0, T1, m);      // T1 = V1^T V1
     k_rr_mm<<<gmm, 256, 0, s>>>(V1, 0, T1, -0.5, 1.5, V2, m);     // V2 = V1 (3I - T1) / 2
     k_rr_mm<<<gmm, 256, 0, s>>>(V2, 1, V2, 1.0, 0.0, T1, m);
@@ -1334,7 +1339,11 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     nl += 7;
     cudaError_t r;
     if ((r = cudaGetLastError())) return r;
-    if ((r = launch_jacobi(V2, m, T1, B.th, B.flag, B.sweeps, P, s))) return r;   // T1 = W'
+    // H' comes from two FP64 products: its entries carry rounding noise of
+    // about m u ||H|| (2^-46 at m = 72), so entries below 2^-44 of its largest
+    // diagonal entry are left alone (their effect on a residual is below
+    // 1e-13 of the largest eigenvalue)
+    if ((r = launch_jacobi(V2, m, T1, B.th, B.flag, B.sweeps, P, s, 44))) return r;   // T1 = W'
     k_rr_mm<<<gmm, 256, 0, s>>>(V1, 0, T1, 1.0, 0.0, B.W, m);     // W = V1 W'
     nl += 2;
     return cudaGetLastError();
@@ -1393,6 +1402,9 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   std::swap(X, Y);
 
   res->converged = false;
+  res->breakdown = 0;
+  res->sweeps64 = 0;
+  res->sweeps32 = 0;
   res->rr = 0;
   res->residual = INFINITY;
   int it = 0;
@@ -1424,13 +1436,16 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       if ((e = cudaMemcpy2DAsync(hth.data(), sizeof(double) * m, B.th.at(0), sizeof(double) * L.per,
                                  sizeof(double) * m, P, cudaMemcpyDeviceToHost, s)))
         return e;
-      int hflag[2];
+      int hflag[4];
       if ((e = cudaMemcpyAsync(hflag, B.flag, sizeof(hflag), cudaMemcpyDeviceToHost, s))) return e;
       if ((e = cudaStreamSynchronize(s))) return e;
       double worst = 0.0;
       for (double v : hres) worst = std::max(worst, std::isfinite(v) ? v : INFINITY);
       res->residual = worst;
-      if (hflag[0]) break;          // factorisation breakdown: let the caller fall back
+      res->breakdown = hflag[0];
+      res->sweeps64 = hflag[2];
+      res->sweeps32 = hflag[3];
+      if (hflag[0]) break;          // breakdown: reported to the caller
       // Converged at the bound, or at the accuracy floor of G: a residual
       // below the floor that no longer halves between two Rayleigh-Ritz
       // steps cannot be improved by more iterations (the exact-slice products

@@ -53,6 +53,9 @@ struct SiResult {
   int rr;               // Rayleigh-Ritz solves performed
   double residual;      // max over problems and i < k of ||G x_i - theta_i x_i|| / theta_0
   bool converged;
+  int breakdown;        // 0, 1 (a Cholesky factorisation broke down) or 2 (a Jacobi sweep limit)
+  int sweeps64;         // most FP64 Jacobi sweeps of one Rayleigh-Ritz solve
+  int sweeps32;         // most FP32 Jacobi sweeps of one Rayleigh-Ritz solve
 };
 
 // Runs the solver on stream s (synchronises it once per convergence check).

@@ -609,6 +609,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   int spec_n;
   int eig_path = 0, eig_iters = 0;
   double eig_res = 0.0;
+  SiResult r{};
   if (n <= g.D_cut) {
     // nothing is cut (U = I); the spectrum of G_L is still recorded
     CK_CUDA(c, identity_isometry(g.U, n, g.sU, G, st));
@@ -671,7 +672,6 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
         sb.has_warm = true;
         sb.kw = g.kprev[di];
       }
-      SiResult r{};
       CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, c->eig_max_iters, st, &r, &nl));
       eig_path = 2;
       eig_iters = r.iterations;
@@ -680,10 +680,15 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       ok = r.converged;
     }
     pf.launched(HOTRG_ST_EIG, (int)nl);
-    if (!ok)
-      return fail(c, HOTRG_EEIG,
-                  "eigensolver did not reach its residual bound in " + std::to_string(c->eig_max_iters) +
-                      " subspace iterations (residual " + std::to_string(eig_res) + ")");
+    if (!ok) {
+      char why[256];
+      snprintf(why, sizeof(why),
+               "eigensolver stopped without reaching its residual bound: %d of at most %d subspace "
+               "iterations, %d Rayleigh-Ritz steps, residual %.3e, breakdown %d (1 Cholesky, 2 Jacobi "
+               "sweep limit), Jacobi sweeps FP64 %d / FP32 %d",
+               r.iterations, c->eig_max_iters, r.rr, eig_res, r.breakdown, r.sweeps64, r.sweeps32);
+      return fail(c, HOTRG_EEIG, why);
+    }
     {
       const SiOut o = si_outputs(c->si_work, 2 * G, n, sb.m);
       SelectArgs a{n, Dn, k, 1, o.theta, o.X, g.scal + 2, kScal, g.U, g.sU,
@@ -762,6 +767,9 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   gs.info.eig_path = eig_path;
   gs.info.eig_iters = eig_iters;
   gs.info.eig_residual = eig_res;
+  gs.info.eig_rr = r.rr;
+  gs.info.eig_sweeps = r.sweeps64;
+  gs.info.eig_sweeps32 = r.sweeps32;
   gs.spec_count = spec_n;
   gs.n = n;
   gs.dn = Dn;
