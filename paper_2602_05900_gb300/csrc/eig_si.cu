@@ -23,6 +23,8 @@
 // iteration stops when ||G x_i - theta_i x_i|| <= tol * theta_0 for i < k; the
 // next check is scheduled from the observed Ritz-value ratio theta_m / theta_k.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -1379,9 +1381,22 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   // where the columns are nearly dependent; large batches use shifted
   // CholeskyQR3 in FP64, which keeps more of the ill-conditioned directions and
   // saves iterations on their hardest problems.
+  //
+  // A block that holds numerically null directions of G (Ritz values below
+  // 1e-9 of the largest: rank-deficient environments at fixed points and in
+  // limits such as the classical Ising chain) cannot be orthogonalised in FP32:
+  // each FP32 pass leaves about 1e-7 of the dominant directions in the null
+  // columns, and the next product amplifies it by theta_0 / sigma (~1e12), so
+  // the basis collapses.  Once a Rayleigh-Ritz step sees such directions, the
+  // rest of the solve orthogonalises with two FP64 CholeskyQR passes.
   const bool fp64_start = P > kSiSmallBatch;
+  bool orth64 = false;
   auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) -> cudaError_t {
     cudaError_t r;
+    if (orth64) {
+      if ((r = cholqr64(src, tmp, shift))) return r;
+      return cholqr64(tmp, dst, 0.0);
+    }
     if (after_rr || !fp64_start) {
       if ((r = cholqr32(src, tmp, 0.0f))) return r;
       return cholqr32(tmp, dst, 0.0f);
@@ -1412,11 +1427,16 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   // the first one goes where the caller expects convergence.
   int next_check = fp64_start ? 3 : std::max(3, b.first_check);
   std::vector<double> hres((size_t)P * k), hth((size_t)P * m);
+  // HOTRG_TRACE_EIG=1 (or 2, with every residual and Ritz value) prints each
+  // convergence check of the solve to stderr
+  static const int trace = getenv("HOTRG_TRACE_EIG") ? atoi(getenv("HOTRG_TRACE_EIG")) : 0;
   double prev_worst = INFINITY;
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
     if (check) {                    // the Rayleigh-Ritz step needs an FP64-orthonormal basis
-      if ((e = polish(X, Z)) || (e = polish(Z, X))) return e;
+      // an FP64 CholeskyQR pass (any conditioning the shift allows) and one
+      // Newton-Schulz step: orthonormal to FP64 accuracy
+      if ((e = cholqr64(X, Z, shift)) || (e = polish(Z, X))) return e;
     }
     if ((e = gemm(X, Y))) return e;  // Y = G X
     ++it;
@@ -1440,8 +1460,31 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       if ((e = cudaMemcpyAsync(hflag, B.flag, sizeof(hflag), cudaMemcpyDeviceToHost, s))) return e;
       if ((e = cudaStreamSynchronize(s))) return e;
       double worst = 0.0;
-      for (double v : hres) worst = std::max(worst, std::isfinite(v) ? v : INFINITY);
+      int wp = 0, wi = 0;
+      for (int q = 0; q < P * k; ++q) {
+        const double v = std::isfinite(hres[q]) ? hres[q] : INFINITY;
+        if (v > worst) {
+          worst = v;
+          wp = q / k;
+          wi = q % k;
+        }
+      }
       res->residual = worst;
+      if (trace) {
+        const double *th = hth.data() + (size_t)wp * m;
+        fprintf(stderr,
+                "[hotrg eig] n %d m %d k %d P %d it %d rr %d worst %.3e at problem %d pair %d: "
+                "theta_i/theta_0 %.6e theta_k/theta_0 %.6e theta_m/theta_0 %.6e sweeps %d/%d flag %d\n",
+                n, m, k, P, it, res->rr, worst, wp, wi, th[wi] / th[0], th[k - 1] / th[0],
+                th[m - 1] / th[0], hflag[3], hflag[2], hflag[0]);
+        if (trace > 1) {
+          fprintf(stderr, "[hotrg eig]   residuals:");
+          for (int i = 0; i < k; ++i) fprintf(stderr, " %.1e", hres[(size_t)wp * k + i]);
+          fprintf(stderr, "\n[hotrg eig]   theta/theta_0:");
+          for (int i = 0; i < m; ++i) fprintf(stderr, " %.4e", th[i] / th[0]);
+          fprintf(stderr, "\n");
+        }
+      }
       res->breakdown = hflag[0];
       res->sweeps64 = hflag[2];
       res->sweeps32 = hflag[3];
@@ -1463,6 +1506,10 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
         break;
       }
       prev_worst = worst;
+      for (int p = 0; p < P && !orth64; ++p) {
+        const double t0 = hth[(size_t)p * m], tm = hth[(size_t)p * m + m - 1];
+        if (!(fabs(tm) > 1e-9 * fabs(t0))) orth64 = true;
+      }
       // Errors in the wanted Ritz pairs shrink by about theta_m / theta_k per
       // iteration: schedule the next check where that predicts convergence.
       double rho = 0.0;
