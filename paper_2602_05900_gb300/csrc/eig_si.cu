@@ -174,6 +174,22 @@ __global__ void k_si_shift_add(PSet Y, PSet X, PSet sig, long long nm) {
   if (blockIdx.x == 0 && threadIdx.x == 0) sig.at(z)[0] = sg;
 }
 
+// After a Rayleigh-Ritz step (Ritz values theta of G + sig[0] I, descending):
+// an environment built with reduced-precision products is indefinite at its
+// rounding level, and the iteration, which converges to the eigenvalues of
+// largest magnitude, would spend block columns on its negative noise
+// directions.  The next products use sig[1] = max(sig[1], 1.5 |lambda_min|) with
+// lambda_min = theta_{m-1} - sig[0] the lowest Ritz value of G, so that G +
+// sig[1] I is positive definite; pairs inside the shift band are not held to
+// the residual bound (their vectors are noise).
+__global__ void k_si_sigma_raise(PSet theta, PSet sig, int m) {
+  const int z = blockIdx.z;
+  if (threadIdx.x == 0) {
+    const double lmin = theta.at(z)[m - 1] - sig.at(z)[0];
+    if (lmin < 0.0 && isfinite(lmin)) sig.at(z)[1] = fmax(sig.at(z)[1], -1.5 * lmin);
+  }
+}
+
 // theta_z[i] -= sig[0] for i < m (the shift of the last Rayleigh-Ritz step)
 __global__ void k_si_unshift(PSet theta, PSet sig, int m) {
   const int z = blockIdx.z;
@@ -1449,6 +1465,10 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       std::swap(Y, Z);
       k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, B.sig, b.has_trace ? 1 : 0, n, k);
       nl += 2;
+      if (b.has_trace) {
+        k_si_sigma_raise<<<dim3(1, 1, P), 32, 0, s>>>(B.th, B.sig, m);
+        nl += 1;
+      }
       ++res->rr;
       if ((e = cudaMemcpy2DAsync(hres.data(), sizeof(double) * k, B.res.at(0), sizeof(double) * L.per,
                                  sizeof(double) * k, P, cudaMemcpyDeviceToHost, s)))
