@@ -49,7 +49,7 @@ constexpr int kCholPanel = 8;      // columns per panel of the blocked FP32 Chol
 constexpr double kXsSmallWork = 32.0 * 1024 * 1024;   // FP64 FMAs of one n x m x m product batch
 constexpr int kSiSmallBatch = 8;      // problems up to which the solve is latency bound
 constexpr double kSiFloorTol = 1e-10;  // residuals accepted once they stop decreasing
-constexpr int kSiSlowIters = 16;       // iterations after which a residual below the floor is accepted
+constexpr int kSiSlowIters = 24;       // iterations after which a residual below the floor is accepted
 constexpr float kChol32Retry = 0x1.0p-12f;   // diagonal shift of a retried FP32 CholeskyQR pass
 
 
@@ -172,22 +172,6 @@ __global__ void k_si_shift_add(PSet Y, PSet X, PSet sig, long long nm) {
        e += (long long)gridDim.x * blockDim.x)
     Y.at(z)[e] = fma(sg, X.at(z)[e], Y.at(z)[e]);
   if (blockIdx.x == 0 && threadIdx.x == 0) sig.at(z)[0] = sg;
-}
-
-// After a Rayleigh-Ritz step (Ritz values theta of G + sig[0] I, descending):
-// an environment built with reduced-precision products is indefinite at its
-// rounding level, and the iteration, which converges to the eigenvalues of
-// largest magnitude, would spend block columns on its negative noise
-// directions.  The next products use sig[1] = max(sig[1], 1.5 |lambda_min|) with
-// lambda_min = theta_{m-1} - sig[0] the lowest Ritz value of G, so that G +
-// sig[1] I is positive definite; pairs inside the shift band are not held to
-// the residual bound (their vectors are noise).
-__global__ void k_si_sigma_raise(PSet theta, PSet sig, int m) {
-  const int z = blockIdx.z;
-  if (threadIdx.x == 0) {
-    const double lmin = theta.at(z)[m - 1] - sig.at(z)[0];
-    if (lmin < 0.0 && isfinite(lmin)) sig.at(z)[1] = fmax(sig.at(z)[1], -1.5 * lmin);
-  }
 }
 
 // theta_z[i] -= sig[0] for i < m (the shift of the last Rayleigh-Ritz step)
@@ -507,10 +491,17 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol(PSet Cin, int m, doubl
     d[j] = (cjj > 0.0 && isfinite(cjj)) ? rsqrt_fp64(cjj) : 1.0;   // 1 / column norm
   }
   __syncthreads();
-  for (int a = ty; a < m; a += 16)
-    for (int b = tx; b < m; b += 16) C[a * ld + b] = C[a * ld + b] * (d[a] * d[b]) + (a == b ? shift : 0.0);
-  __syncthreads();
   __shared__ int bad;
+  // Nearly dependent columns break the factorisation: later attempts add a
+  // larger diagonal shift (2^-26, then 2^-12 of the unit diagonal), which
+  // always succeeds and leaves a basis the next pass finishes.
+  for (int attempt = 0; attempt < 3; ++attempt) {
+  const double shv = attempt == 0 ? shift : fmax(shift, attempt == 1 ? 0x1.0p-26 : 0x1.0p-12);
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) C[(e / m) * ld + e % m] = Cin.at(z)[e];
+  __syncthreads();
+  for (int a = ty; a < m; a += 16)
+    for (int b = tx; b < m; b += 16) C[a * ld + b] = C[a * ld + b] * (d[a] * d[b]) + (a == b ? shv : 0.0);
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   // right-looking Cholesky on the upper triangle
@@ -533,6 +524,8 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol(PSet Cin, int m, doubl
     __syncthreads();
   }
   __syncthreads();
+  if (!bad) break;
+  }
   if (bad) {
     if (threadIdx.x == 0) atomicExch(flag, 1);
     return;
@@ -1465,10 +1458,6 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       std::swap(Y, Z);
       k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, B.sig, b.has_trace ? 1 : 0, n, k);
       nl += 2;
-      if (b.has_trace) {
-        k_si_sigma_raise<<<dim3(1, 1, P), 32, 0, s>>>(B.th, B.sig, m);
-        nl += 1;
-      }
       ++res->rr;
       if ((e = cudaMemcpy2DAsync(hres.data(), sizeof(double) * k, B.res.at(0), sizeof(double) * L.per,
                                  sizeof(double) * k, P, cudaMemcpyDeviceToHost, s)))

@@ -28,8 +28,10 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hotrg.h"
@@ -234,7 +236,18 @@ struct Group {
   // steady-state run replays two graphs per segment.
   std::map<std::array<long long, 7>, SegGraph> graphs;
   std::set<std::array<long long, 7>> seen, nograph;
+  // Work of the group's steps: its own stream (the context's stream when the
+  // context holds one group), stage profiler and eigensolver workspace, so
+  // that the groups of a batch can step concurrently.
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Profiler prof;
+  double *si_work = nullptr;
   ~Group() {
+    if (own_stream && stream) {
+      cudaStreamSynchronize(stream);
+      cudaStreamDestroy(stream);
+    }
     for (auto &kv : graphs) {
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
       for (auto &iv : kv.second.events) {
@@ -248,14 +261,15 @@ struct Group {
 }  // namespace
 
 struct hotrg_ctx {
-  Profiler prof;
+  bool prof_on = false;                     // stage profiler enabled
+  int prof_steps = 0;                       // steps taken while it was on
+  std::mutex mu;                            // guards status/msg (groups step on their own threads)
   cudaStream_t stream = nullptr;
   hotrg_prec prec = HOTRG_FP64;
   int nsteps = 0;
   int n_inst = 0;
   std::vector<std::unique_ptr<Group>> groups;
   std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
-  double *si_work = nullptr;                // eigensolver workspace, shared by the groups
   bool eig_tc = true;                       // exact-slice tensor-core products G X
   bool use_graphs = true;                   // replay contraction segments as CUDA graphs
   int xs_digits = 6;                        // digits of the exact-slice contraction mode
@@ -269,7 +283,9 @@ struct hotrg_ctx {
 namespace {
 
 hotrg_status fail(hotrg_ctx *c, hotrg_status s, const std::string &m) {
-  if (c && c->status == HOTRG_OK) {
+  if (!c) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->status == HOTRG_OK) {
     c->status = s;
     c->msg = m;
   }
@@ -375,7 +391,7 @@ hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
   } else {
     g.sC1 = round_up(nmax, 32);
     if ((s = dalloc(c, &g.c1, 6 * g.sC1 * G))) return s;
-    const int r = g.tc.init(c->prec, g.D0, g.D_cut, G, c->stream, c->err);
+    const int r = g.tc.init(c->prec, g.D0, g.D_cut, G, g.stream, c->err);
     if (r == 2) return fail(c, HOTRG_ENOMEM, "tensor-core operand buffers do not fit");
     if (r) return fail(c, HOTRG_ECUDA, "tensor-core path initialisation failed");
   }
@@ -402,7 +418,6 @@ hotrg_status create_ctx(int n, const double *const *T0s, const int *D0s, const i
     return s;
   };
   c->stream = static_cast<cudaStream_t>(stream);
-  c->prof.stream = c->stream;
   c->prec = prec;
   c->n_inst = n;
   c->where.resize(n);
@@ -426,15 +441,24 @@ hotrg_status create_ctx(int n, const double *const *T0s, const int *D0s, const i
   }
   hotrg_status s;
   if ((s = dalloc(c, &c->err, 4))) return bail(s);
-  long long si_doubles = 0;
   for (auto &gp : c->groups) {
     Group &g = *gp;
     g.G = (int)g.members.size();
+    if (c->groups.size() == 1) {
+      g.stream = c->stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bail(HOTRG_ECUDA);
+      }
+      g.own_stream = true;
+    }
+    g.prof.stream = g.stream;
     if ((s = alloc_group(c, g))) return bail(s);
     const int nsi = std::max(g.Dm * g.Dm, kSiMaxBlock + 1);
-    si_doubles = std::max(si_doubles, si_workspace_doubles(2 * g.G, nsi, kSiMaxBlock));
+    if ((s = dalloc(c, &g.si_work, (size_t)si_workspace_doubles(2 * g.G, nsi, kSiMaxBlock))))
+      return bail(s);
   }
-  if ((s = dalloc(c, &c->si_work, (size_t)si_doubles))) return bail(s);
   if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) return bail(HOTRG_ECUDA);
   for (auto &gp : c->groups) {
     Group &g = *gp;
@@ -461,8 +485,8 @@ hotrg_status create_ctx(int n, const double *const *T0s, const int *D0s, const i
 
 // One step of every instance of group g (see the file comment).
 hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
-  cudaStream_t st = c->stream;
-  Profiler &pf = c->prof;
+  cudaStream_t st = g.stream;
+  Profiler &pf = g.prof;
   const int G = g.G;
 
   // ---- the step's view of the stored tensor T[x,x',y,y'] (shape dx,dx,dy,dy)
@@ -620,8 +644,8 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     sb.m = jacobi_block(n);
     sb.G = pset_linear(g.GL, g.sT);
     long long nl = 0;
-    CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
-    const SiOut o = si_outputs(c->si_work, G, n, sb.m);
+    CK_CUDA(c, jacobi_full(sb, g.si_work, st, &nl));
+    const SiOut o = si_outputs(g.si_work, G, n, sb.m);
     CK_CUDA(c, spectrum_no_cut(o.theta, n, 1, g.scal + 2, kScal, rec, g.sRec, spec, g.sSpec, G, st));
     pf.launched(HOTRG_ST_EIG, 2 + (int)nl);
     spec_n = n;
@@ -637,7 +661,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     bool ok = false;
     if (n + (n & 1) <= kSiMaxBlock) {
       sb.m = jacobi_block(n);
-      CK_CUDA(c, jacobi_full(sb, c->si_work, st, &nl));
+      CK_CUDA(c, jacobi_full(sb, g.si_work, st, &nl));
       eig_path = 1;
       ok = true;
     } else {
@@ -654,11 +678,11 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       // about the operands' unit roundoff u (TF32 2^-11, two-term BF16 ~2^-17,
       // three-term ~2^-24): eigenvalues below that level relative to the
       // largest are noise, with eigenvectors undetermined beyond it, so a
-      // residual that stalls there is accepted (20 u; FP64-grade G: 1e-10).
+      // residual that stalls there is accepted (2 u; FP64-grade G: 1e-10).
       switch (c->prec) {
-        case HOTRG_TF32: sb.floor_tol = 20.0 * 0x1.0p-11; break;
-        case HOTRG_BF16X3: sb.floor_tol = 20.0 * 0x1.0p-17; break;
-        case HOTRG_BF16X6: sb.floor_tol = 20.0 * 0x1.0p-24; break;
+        case HOTRG_TF32: sb.floor_tol = 2.0 * 0x1.0p-11; break;
+        case HOTRG_BF16X3: sb.floor_tol = 2.0 * 0x1.0p-17; break;
+        case HOTRG_BF16X6: sb.floor_tol = 2.0 * 0x1.0p-24; break;
         default: sb.floor_tol = 0.0; break;
       }
       // the solve of the last step in this direction took iters_prev
@@ -672,7 +696,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
         sb.has_warm = true;
         sb.kw = g.kprev[di];
       }
-      CK_CUDA(c, si_solve(sb, c->si_work, 1e-12, c->eig_max_iters, st, &r, &nl));
+      CK_CUDA(c, si_solve(sb, g.si_work, 1e-12, c->eig_max_iters, st, &r, &nl));
       eig_path = 2;
       eig_iters = r.iterations;
       g.iters_prev[di] = r.converged ? r.iterations : 0;
@@ -690,7 +714,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       return fail(c, HOTRG_EEIG, why);
     }
     {
-      const SiOut o = si_outputs(c->si_work, 2 * G, n, sb.m);
+      const SiOut o = si_outputs(g.si_work, 2 * G, n, sb.m);
       SelectArgs a{n, Dn, k, 1, o.theta, o.X, g.scal + 2, kScal, g.U, g.sU,
                    rec, g.sRec, spec, g.sSpec, G};
       CK_CUDA(c, select_isometry(a, st));
@@ -897,6 +921,8 @@ hotrg_status hotrg_xxz_tensor(double Jxy, double Jz, double tau, double *T0_out)
 void hotrg_destroy(hotrg_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (auto &g : c->groups)
+    if (g->own_stream && g->stream) cudaStreamSynchronize(g->stream);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -916,13 +942,33 @@ hotrg_status hotrg_step(hotrg_ctx *c, hotrg_dir dir) {
   if (c->status != HOTRG_OK) return c->status;
   if (dir != HOTRG_DIR_X && dir != HOTRG_DIR_Y) return HOTRG_EINVAL;
   if (c->nsteps >= kMaxSteps) return fail(c, HOTRG_ESTATE, "step limit reached");
-  for (auto &g : c->groups)
-    if (hotrg_status s = step_group(c, *g, dir, c->nsteps)) return s;
-  // one synchronisation per step: device errors of this step surface here
-  CK_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->prof.collect(false);
+  if (c->groups.size() == 1) {
+    if (hotrg_status s = step_group(c, *c->groups[0], dir, c->nsteps)) return s;
+    // one synchronisation per step: device errors of this step surface here
+    CK_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else {
+    // The cut groups of a batch step concurrently: each on its own host thread
+    // and stream (their eigensolvers are latency-bound chains that leave most
+    // SMs idle), ordered after the work already on the context's stream.
+    cudaEvent_t start = nullptr;
+    CK_CUDA(c, cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    CK_CUDA(c, cudaEventRecord(start, c->stream));
+    for (auto &g : c->groups) CK_CUDA(c, cudaStreamWaitEvent(g->stream, start, 0));
+    std::vector<hotrg_status> st(c->groups.size(), HOTRG_OK);
+    std::vector<std::thread> th;
+    th.reserve(c->groups.size());
+    const int step = c->nsteps;
+    for (size_t i = 0; i < c->groups.size(); ++i)
+      th.emplace_back([c, &st, i, dir, step] { st[i] = step_group(c, *c->groups[i], dir, step); });
+    for (auto &t : th) t.join();
+    cudaEventDestroy(start);
+    for (auto &g : c->groups) CK_CUDA(c, cudaStreamSynchronize(g->stream));
+    for (hotrg_status s : st)
+      if (s != HOTRG_OK) return c->status != HOTRG_OK ? c->status : s;
+  }
+  for (auto &g : c->groups) g->prof.collect(false);
   if (hotrg_status fs = check_flag(c)) return fs;
-  if (c->prof.on) c->prof.acc.steps += 1;
+  if (c->prof_on) c->prof_steps += 1;
   c->nsteps += 1;
   return HOTRG_OK;
 }
@@ -991,8 +1037,13 @@ hotrg_status hotrg_profile_enable(hotrg_ctx *c, int enable) {
   if (!c) return HOTRG_EINVAL;
   if (c->status != HOTRG_OK) return c->status;
   CK_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->prof.reset();
-  c->prof.on = enable != 0;
+  for (auto &g : c->groups) {
+    CK_CUDA(c, cudaStreamSynchronize(g->stream));
+    g->prof.reset();
+    g->prof.on = enable != 0;
+  }
+  c->prof_on = enable != 0;
+  c->prof_steps = 0;
   return HOTRG_OK;
 }
 
@@ -1000,8 +1051,20 @@ hotrg_status hotrg_profile_read(hotrg_ctx *c, hotrg_profile_t *out) {
   if (!c || !out) return HOTRG_EINVAL;
   if (c->status != HOTRG_OK) return c->status;
   CK_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->prof.collect(true);
-  *out = c->prof.acc;
+  hotrg_profile_t sum{};
+  for (auto &g : c->groups) {
+    CK_CUDA(c, cudaStreamSynchronize(g->stream));
+    g->prof.collect(true);
+    const hotrg_profile_t &a = g->prof.acc;
+    sum.launches += a.launches;
+    for (int k = 0; k < HOTRG_NSTAGES; ++k) {
+      sum.stage_launches[k] += a.stage_launches[k];
+      sum.ms[k] += a.ms[k];
+      sum.flops[k] += a.flops[k];
+    }
+  }
+  sum.steps = c->prof_steps;
+  *out = sum;
   return HOTRG_OK;
 }
 
