@@ -110,3 +110,45 @@ def test_clock_summary_reports_cycles_per_step():
     out = s.summary(ms_per_step=2.0)
     assert out["sm_mhz"] == 2065.0 and out["reasons"] == ["sw_power_cap"]
     assert out["mcycles_per_step"] == round(2.0 * 2065.0 / 1e3, 4)
+
+
+def test_sweep_partition_is_a_balanced_cover():
+    from workloads import sweep256
+    models = sweep256()
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.partition_instances(models, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(models)))
+        loads = [sum(2.0 * models[i].D_cut ** 7 for i in p) for p in parts]
+        # longest-processing-time first: no rank carries more than the mean plus one instance
+        assert max(loads) - sum(loads) / world <= 2.0 * 40 ** 7 + 1e-6
+
+
+def _sweep_rank(rank, world, port, out):
+    import torch.distributed as dist
+    from workloads import sweep256
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    models = sweep256()
+    mine = bench.partition_instances(models, world)[rank]
+    got = bench.gather_floats([float(i) for i in mine], world)
+    out[rank] = got
+    dist.destroy_process_group()
+
+
+def test_sweep_shards_gather_over_two_gloo_ranks():
+    """Each rank derives its own share of the sweep with no communication; the
+    only exchange is the host gather after the timed region, which must hand
+    every rank every instance exactly once."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = 29600 + os.getpid() % 1000
+    procs = [ctx.Process(target=_sweep_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        assert sorted(int(v) for v in out[r]) == list(range(256))
