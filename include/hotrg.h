@@ -55,7 +55,11 @@ typedef enum {
   HOTRG_EEIG = 4,        /* the eigensolver did not converge or rejected its input    */
   HOTRG_ENONFINITE = 5,  /* max-norm or trace is zero, negative or not finite         */
   HOTRG_ETIMEOUT = 6,    /* a bounded device wait ran out                            */
-  HOTRG_ESTATE = 7       /* call not valid in the context's current state            */
+  HOTRG_ESTATE = 7,      /* call not valid in the context's current state            */
+  HOTRG_EBOUNDS = 8      /* a mapped index fell outside its buffer: reported only by a
+                            library built with -DHOTRG_CHECKED=1 (bounds-checked build,
+                            in which every mapped access of the GEMM, gather and epilogue
+                            kernels is checked, and a bad one skipped, not performed) */
 } hotrg_status;
 
 typedef enum { HOTRG_DIR_X = 0, HOTRG_DIR_Y = 1 } hotrg_dir;

@@ -14,11 +14,12 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhotrg.so")
+# HOTRG_LIB selects another build of the library (the bounds-checked one)
+LIB_PATH = os.environ.get("HOTRG_LIB") or os.path.join(HERE, "libhotrg.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hotrg.h")
 
 HOTRG_OK, HOTRG_EINVAL, HOTRG_ENOMEM, HOTRG_ECUDA, HOTRG_EEIG, HOTRG_ENONFINITE, \
-    HOTRG_ETIMEOUT, HOTRG_ESTATE = range(8)
+    HOTRG_ETIMEOUT, HOTRG_ESTATE, HOTRG_EBOUNDS = range(9)
 DIR_X, DIR_Y = 0, 1
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3, "bf16xs": 4}
 

@@ -60,8 +60,31 @@ struct StageHook {
   virtual ~StageHook() {}
 };
 
+// Bounds-checked build (-DHOTRG_CHECKED=1, the stand-in for memory sanitizers):
+// every mapped access of the GEMM, gather and epilogue kernels is compared
+// with the capacity of its buffer; an access outside it is skipped and
+// recorded in the context's device error flag as 3 (reported as
+// HOTRG_EBOUNDS).  A capacity of 0 means "not known" (no check).  The normal
+// build compiles the checks away.
+#ifdef HOTRG_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool checked_ok(long long off, long long cap, int *err) {
+  if constexpr (kChecked) {
+    if (cap > 0 && (off < 0 || off >= cap)) {
+      if (err) atomicMax(err, 3);
+      return false;
+    }
+  }
+  return true;
+}
+
 // C(m, n) = sum_k A(m, k) * B(n, k) over mapped operands, for `batch`
-// instances whose operands lie bA, bB, bC elements apart.
+// instances whose operands lie bA, bB, bC elements apart.  capA, capB, capC:
+// elements of each buffer from its base (all instances; 0 = unknown), used by
+// the checked build, which records violations in *err.
 struct MappedGemm {
   int M, N, K;
   const double *A;
@@ -72,6 +95,8 @@ struct MappedGemm {
   IdxMap cm, cn;
   int batch;
   long long bA, bB, bC;
+  long long capA = 0, capB = 0, capC = 0;
+  int *err = nullptr;
 };
 
 // gemm_f64.cu

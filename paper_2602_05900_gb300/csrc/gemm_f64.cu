@@ -26,9 +26,10 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(MappedGemm g) {
   const long long m0 = (long long)blockIdx.x * BM;
   const long long n0 = (long long)blockIdx.y * BN;
   // instance of the batch
-  g.A += blockIdx.z * g.bA;
-  g.B += blockIdx.z * g.bB;
-  g.C += blockIdx.z * g.bC;
+  const long long zA = blockIdx.z * g.bA, zB = blockIdx.z * g.bB, zC = blockIdx.z * g.bC;
+  g.A += zA;
+  g.B += zB;
+  g.C += zC;
 
   if (tid < BM) {
     long long m = m0 + tid;
@@ -59,10 +60,10 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(MappedGemm g) {
       int r, k;
       if (K_FAST_A) { r = e / BK; k = e % BK; } else { r = e % BM; k = e / BM; }
       long long ro = rowA[r], ko = kA[buf][k];
-      ra[i] = (ro >= 0 && ko >= 0) ? g.A[ro + ko] : 0.0;
+      ra[i] = (ro >= 0 && ko >= 0 && checked_ok(zA + ro + ko, g.capA, g.err)) ? g.A[ro + ko] : 0.0;
       if (K_FAST_B) { r = e / BK; k = e % BK; } else { r = e % BN; k = e / BN; }
       ro = rowB[r]; ko = kB[buf][k];
-      rb[i] = (ro >= 0 && ko >= 0) ? g.B[ro + ko] : 0.0;
+      rb[i] = (ro >= 0 && ko >= 0 && checked_ok(zB + ro + ko, g.capB, g.err)) ? g.B[ro + ko] : 0.0;
     }
   };
   auto store_regs = [&](int buf, const double ra[4], const double rb[4]) {
@@ -122,7 +123,10 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(MappedGemm g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       long long n = n0 + tx + 16 * j;
-      if (n < g.N) g.C[co + map_off(g.cn, n)] = acc[i][j];
+      if (n < g.N) {
+        const long long off = co + map_off(g.cn, n);
+        if (checked_ok(zC + off, g.capC, g.err)) g.C[off] = acc[i][j];
+      }
     }
   }
 }
@@ -134,20 +138,24 @@ __global__ void __launch_bounds__(NT) k_dot_f64(MappedGemm g) {
   __shared__ double red[NT];
   const long long e = blockIdx.x;
   const long long m = e / g.N, n = e % g.N;
-  g.A += blockIdx.z * g.bA;
-  g.B += blockIdx.z * g.bB;
-  g.C += blockIdx.z * g.bC;
+  const long long zA = blockIdx.z * g.bA, zB = blockIdx.z * g.bB, zC = blockIdx.z * g.bC;
+  g.A += zA;
+  g.B += zB;
+  g.C += zC;
   const long long ao = map_off(g.am, m), bo = map_off(g.bn, n);
   double v = 0.0;
-  for (int k = threadIdx.x; k < g.K; k += NT)
-    v = fma(g.A[ao + map_off(g.ak, k)], g.B[bo + map_off(g.bk, k)], v);
+  for (int k = threadIdx.x; k < g.K; k += NT) {
+    const long long oa = ao + map_off(g.ak, k), ob = bo + map_off(g.bk, k);
+    if (checked_ok(zA + oa, g.capA, g.err) && checked_ok(zB + ob, g.capB, g.err)) v = fma(g.A[oa], g.B[ob], v);
+  }
   red[threadIdx.x] = v;
   __syncthreads();
   for (int w = NT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) g.C[map_off(g.cm, m) + map_off(g.cn, n)] = red[0];
+  const long long oc = map_off(g.cm, m) + map_off(g.cn, n);
+  if (threadIdx.x == 0 && checked_ok(zC + oc, g.capC, g.err)) g.C[oc] = red[0];
 }
 
 constexpr long long kDotMaxOutputs = 64, kDotMinK = 256;
@@ -163,9 +171,10 @@ __global__ void __launch_bounds__(256) k_gemm_f64_small(MappedGemm g) {
   __shared__ double As[ST][ST + 1], Bs[ST][ST + 1];   // [k][row]
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long long m0 = (long long)blockIdx.x * ST, n0 = (long long)blockIdx.y * ST;
-  g.A += blockIdx.z * g.bA;
-  g.B += blockIdx.z * g.bB;
-  g.C += blockIdx.z * g.bC;
+  const long long zA = blockIdx.z * g.bA, zB = blockIdx.z * g.bB, zC = blockIdx.z * g.bC;
+  g.A += zA;
+  g.B += zB;
+  g.C += zC;
   // loads: thread (ty, tx) brings A(m0 + ty, k0 + tx) and B(n0 + ty, k0 + tx)
   const long long ar = (m0 + ty < g.M) ? map_off(g.am, m0 + ty) : -1;
   const long long br = (n0 + ty < g.N) ? map_off(g.bn, n0 + ty) : -1;
@@ -173,15 +182,19 @@ __global__ void __launch_bounds__(256) k_gemm_f64_small(MappedGemm g) {
   for (int k0 = 0; k0 < g.K; k0 += ST) {
     const int k = k0 + tx;
     const bool kv = k < g.K;
-    As[tx][ty] = (ar >= 0 && kv) ? g.A[ar + map_off(g.ak, k)] : 0.0;
-    Bs[tx][ty] = (br >= 0 && kv) ? g.B[br + map_off(g.bk, k)] : 0.0;
+    const long long oa = ar + (kv ? map_off(g.ak, k) : 0), ob = br + (kv ? map_off(g.bk, k) : 0);
+    As[tx][ty] = (ar >= 0 && kv && checked_ok(zA + oa, g.capA, g.err)) ? g.A[oa] : 0.0;
+    Bs[tx][ty] = (br >= 0 && kv && checked_ok(zB + ob, g.capB, g.err)) ? g.B[ob] : 0.0;
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < ST; ++kk) acc = fma(As[kk][ty], Bs[kk][tx], acc);
     __syncthreads();
   }
   const long long m = m0 + ty, n = n0 + tx;
-  if (m < g.M && n < g.N) g.C[map_off(g.cm, m) + map_off(g.cn, n)] = acc;
+  if (m < g.M && n < g.N) {
+    const long long oc = map_off(g.cm, m) + map_off(g.cn, n);
+    if (checked_ok(zC + oc, g.capC, g.err)) g.C[oc] = acc;
+  }
 }
 
 }  // namespace

@@ -329,12 +329,15 @@ void tensor_from_sqrt(int q, const double *W, const double *w, double *T0) {
 }
 
 // Reads the device error flag after a synchronisation: 1 = a max-norm was zero
-// or not finite, 2 = a bounded device wait ran out.
+// or not finite, 2 = a bounded device wait ran out, 3 = an index outside its
+// buffer (bounds-checked build only).
 hotrg_status check_flag(hotrg_ctx *c) {
   int herr = 0;
   if (cudaMemcpy(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(c, HOTRG_ECUDA, "reading the device error flag failed");
   if (herr == 1) return fail(c, HOTRG_ENONFINITE, "max-norm of a coarse-grained tensor was zero or not finite");
+  if (herr == 3)
+    return fail(c, HOTRG_EBOUNDS, "a kernel's mapped index fell outside its buffer (bounds-checked build)");
   if (herr) return fail(c, HOTRG_ETIMEOUT, "a tensor-core kernel's bounded wait ran out");
   return HOTRG_OK;
 }
@@ -606,6 +609,9 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
     for (const Part &p : parts) {
       MappedGemm m{(int)DE, (int)DE, (int)DE, g.T, p.row, p.red, g.T, p.row, p.red, p.dst, out_m,
                    out_n, G, g.sT, g.sT, sPart};
+      m.capA = m.capB = g.sT * G;
+      m.capC = sPart * G;
+      m.err = c->err;
       CK_CUDA(c, mgemm(m));
     }
     pf.launched(HOTRG_ST_ENV, 4);
@@ -617,6 +623,11 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.GL, gm, gn, G, sPart, sPart, g.sT};
     MappedGemm gr{(int)D2, (int)D2, (int)E2, AR, map1(E2), map1(1), BR, map1(E2), map1(1),
                   g.GR, gm, gn, G, sPart, sPart, g.sT};
+    for (MappedGemm *q : {&gl, &gr}) {
+      q->capA = q->capB = sPart * G;
+      q->capC = g.sT * G;
+      q->err = c->err;
+    }
     CK_CUDA(c, mgemm(gl));
     CK_CUDA(c, mgemm(gr));
     pf.launched(HOTRG_ST_GRAM, 2);
@@ -749,6 +760,10 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.T, map3(E, E, syp, sy, sxp), map1(sx),
                   P, map2(Dn, D2 * E2, E), map3(E, E, 1, DE, DE * E),
                   G, g.sU, g.sT, sPQ};
+    g5.capA = g.sU * G;
+    g5.capB = g.sT * G;
+    g5.capC = sPQ * G;
+    g5.err = c->err;
     CK_CUDA(c, mgemm(g5));
     pf.launched(HOTRG_ST_PROJ_P, 1);
     pf.end(HOTRG_ST_PROJ_P);
@@ -759,6 +774,10 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.T, map2(D, sxp, syp), map2(E, sy, sx),
                   Q, map3(E, D, E * D2, D, E2 * D2), map2(D, 1, D2),
                   G, sPQ, g.sT, sPQ};
+    g6.capA = sPQ * G;
+    g6.capB = g.sT * G;
+    g6.capC = sPQ * G;
+    g6.err = c->err;
     CK_CUDA(c, mgemm(g6));
     pf.launched(HOTRG_ST_PROJ_Q, 1);
     pf.end(HOTRG_ST_PROJ_Q);
@@ -769,6 +788,10 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
                   g.U, map1(n), map1(1),
                   g.Tn, tm, tn,
                   G, sPQ, g.sU, g.sT};
+    g7.capA = sPQ * G;
+    g7.capB = g.sU * G;
+    g7.capC = g.sT * G;
+    g7.err = c->err;
     CK_CUDA(c, mgemm(g7));
     pf.launched(HOTRG_ST_PROJ_T, 1);
     pf.end(HOTRG_ST_PROJ_T);
@@ -857,6 +880,7 @@ const char *hotrg_status_string(hotrg_status s) {
     case HOTRG_ENONFINITE: return "HOTRG_ENONFINITE";
     case HOTRG_ETIMEOUT: return "HOTRG_ETIMEOUT";
     case HOTRG_ESTATE: return "HOTRG_ESTATE";
+    case HOTRG_EBOUNDS: return "HOTRG_EBOUNDS";
   }
   return "HOTRG_UNKNOWN";
 }

@@ -52,7 +52,13 @@ __device__ __forceinline__ float round_tf32(float v) {
   return __uint_as_float(u);
 }
 
-__device__ __forceinline__ void store_out(const TcEpilogue &e, long long off, float v) {
+// Stores v at element off of instance buffer e.C; zoff is that buffer's
+// offset from the base of the whole allocation (bounds of the checked build).
+__device__ __forceinline__ void store_out(const TcEpilogue &e, long long off, float v, long long zoff,
+                                          int *err) {
+  if (!checked_ok(zoff + off, e.cap, err)) return;
+  if (e.kind == OutKind::BF16P && !checked_ok(zoff + off + (e.planes - 1) * e.plane_stride, e.cap, err))
+    return;
   switch (e.kind) {
     case OutKind::F32:
       static_cast<float *>(e.C)[off] = e.round_tf32 ? round_tf32(v) : v;
@@ -272,6 +278,7 @@ __global__ void __launch_bounds__(384, 1)
       tile_coords(t, n0, m0, z);
       TcEpilogue e = epi;
       e.C = static_cast<char *>(epi.C) + (long long)z * epi.bstride * esize;
+      const long long zoff = (long long)z * epi.bstride;
       const int row = m0 + quad * 32 + lane;
       const bool rv = row < M;
       const long long roff = rv ? map_off(e.cm, row) : -1;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const long long co = __shfl_sync(0xffffffffu, coff, j);
-            if (rv && co >= 0) store_out(e, roff + co, __uint_as_float(r[j]));
+            if (rv && co >= 0) store_out(e, roff + co, __uint_as_float(r[j]), zoff, err_flag);
           }
         } else {
 #pragma unroll
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(384, 1)
           for (int rr = 0; rr < 32; ++rr) {
             const long long ro = __shfl_sync(0xffffffffu, roff, rr);
             const float v = stage[rr * 33 + lane];
-            if (ro >= 0 && coff >= 0) store_out(e, ro + coff, v);
+            if (ro >= 0 && coff >= 0) store_out(e, ro + coff, v, zoff, err_flag);
           }
           __syncwarp();
         }

@@ -45,6 +45,8 @@ struct TcEpilogue {
   long long bstride;       // elements between the outputs of consecutive instances
   bool transpose;          // set by tc_gemm: stage through shared memory so that a warp
                            // stores 32 consecutive columns of one row (unit-stride cn)
+  long long cap;           // elements of C from its base, all instances and planes (0 =
+                           // unknown): bounds of the checked build
 };
 
 // Launches C(M x N) = A(M x K) . B(N x K)^T for every instance of the batch

@@ -49,14 +49,17 @@ __device__ __forceinline__ float tf32_rna(float v) {
 // dst[p][r][k] (pitch columns, zero beyond K) = split_p(src[rm(r) + km(k)])
 template <int MODE>
 __global__ void k_gather(const double *src, long long sSrc, int R, int K, int pitch, IdxMap rm,
-                         IdxMap km, void *dst, long long sDst, long long plane_stride) {
-  src += blockIdx.y * sSrc;
+                         IdxMap km, void *dst, long long sDst, long long plane_stride,
+                         long long src_cap, int *err) {
+  const long long zs = blockIdx.y * sSrc;
+  src += zs;
   dst = static_cast<char *>(dst) + blockIdx.y * sDst * (MODE == 0 ? 4 : 2);
   const long long total = (long long)R * pitch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / pitch), k = (int)(e % pitch);
-    const double v = (k < K) ? src[map_off(rm, r) + map_off(km, k)] : 0.0;
+    const long long so = (k < K) ? map_off(rm, r) + map_off(km, k) : 0;
+    const double v = (k < K && checked_ok(zs + so, src_cap, err)) ? src[so] : 0.0;
     if constexpr (MODE == 0) {
       static_cast<float *>(dst)[e] = tf32_rna(static_cast<float>(v));
     } else {
@@ -126,10 +129,11 @@ static cudaError_t gather(const TcPath::Impl &I, const double *src, long long sS
                           int pitch, IdxMap rm, IdxMap km, void *dst) {
   const long long ps = (long long)R * pitch;
   const dim3 g(grid_for(ps, I.G), I.G);
+  const long long cap = sSrc * I.G;
   switch (I.mode) {
-    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps); break;
-    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps); break;
-    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps); break;
+    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps, cap, I.err); break;
+    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps, cap, I.err); break;
+    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps, cap, I.err); break;
   }
   return cudaGetLastError();
 }
@@ -155,10 +159,12 @@ static TcEpilogue operand_epilogue(const TcPath::Impl &I, void *dst, long long p
   e.cm = cm;
   e.cn = cn;
   e.bstride = bstride;
+  e.cap = bstride * I.G;
   return e;
 }
 
-static TcEpilogue f64_epilogue(double *dst, IdxMap cm, IdxMap cn, long long bstride) {
+static TcEpilogue f64_epilogue(const TcPath::Impl &I, double *dst, IdxMap cm, IdxMap cn,
+                               long long bstride) {
   TcEpilogue e{};
   e.kind = OutKind::F64;
   e.C = dst;
@@ -166,6 +172,7 @@ static TcEpilogue f64_epilogue(double *dst, IdxMap cm, IdxMap cn, long long bstr
   e.cm = cm;
   e.cn = cn;
   e.bstride = bstride;
+  e.cap = bstride * I.G;
   return e;
 }
 
@@ -199,7 +206,7 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
   for (int side = 0; side < 2; ++side) {
     TcOperand a = operand(I, I.part[2 * side], D2, E2, p3, I.sTop);
     TcOperand b = operand(I, I.part[2 * side + 1], D2, E2, p3, I.sTop);
-    if (cudaError_t e_ = tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(side ? GR : GL, gm, gn, sG),
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(I, side ? GR : GL, gm, gn, sG),
                                  I.err, I.s))
       return e_;
   }
@@ -256,7 +263,7 @@ int TcPath::project(const double *T, long long sT, const double *U, long long sU
   hook->begin(HOTRG_ST_PROJ_T);
   {
     TcOperand a = operand(I, I.Q, Dn * E2, n, p7, I.sPop), b = operand(I, I.opU7, Dn, n, p7, I.sTop);
-    if (cudaError_t e_ = tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(Tout, tm, tn, sTout),
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, Dn * E2, Dn, n, f64_epilogue(I, Tout, tm, tn, sTout),
                                  I.err, I.s))
       return e_;
   }
