@@ -194,7 +194,12 @@ def test_batched_sweep_subset_vs_stored_oracle(pkg, prec, tol):
 def test_batched_sweep_subset_matches_single_contexts(pkg):
     """One instance per cut group of the sweep subset, batched (TF32) against
     the same instance in a context of its own: same kernels and operand
-    rounding, so they agree far below the TF32 error."""
+    rounding.  A batch shares one convergence decision over all its
+    environments, so an instance can take more subspace iterations than alone;
+    where a TF32 environment has a flat noise tail (low-temperature instances)
+    the solver accepts a residual at the noise floor of G (2 u) after 24
+    iterations, and the two runs then differ at that floor's second order,
+    far below the TF32 error itself (~2e-4): bounded here at 1e-6."""
     models, _ = sweep_rows()
     T0s = [pkg.ising_tensor(m.beta, m.h) for m in models]
     with pkg.HotrgBatch(T0s, [m.D_cut for m in models], "tf32") as bt:
@@ -207,4 +212,4 @@ def test_batched_sweep_subset_matches_single_contexts(pkg):
         with pkg.Hotrg(T0s[i], D, "tf32") as one:
             one.run(models[i].steps)
             single = one.ln_z_per_site()
-        assert abs(lz[i] / single - 1) < 1e-9, (D, lz[i], single)
+        assert abs(lz[i] / single - 1) < 1e-6, (D, lz[i], single)
