@@ -920,6 +920,13 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
 }
 
+// Out = a A + b I for m x m matrices of every problem z.
+__global__ void k_rr_axpi(PSet A, double a, double b, PSet Out, int m) {
+  const int z = blockIdx.z;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)
+    Out.at(z)[e] = a * A.at(z)[e] + ((e % m == e / m) ? b : 0.0);
+}
+
 // Out = op(A) (bs B + bd I) for m x m column-major FP64 matrices of every
 // problem z (op(A) = A^T if ta).  One CTA per 8 x 8 output tile; the sum over
 // k is split four ways across the CTA's threads and combined in a fixed order.
@@ -1309,7 +1316,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     return cudaGetLastError();
   };
   // C = A^T B (m x m), symmetrised; ns: write the Newton-Schulz polish (3I - C)/2 instead
-  auto gram = [&](PSet A, PSet Bm, bool sym, bool f32, bool ns) -> cudaError_t {
+  auto gram = [&](PSet A, PSet Bm, bool sym, bool f32, bool ns, PSet out) -> cudaError_t {
     if (xs_small) {
       const XsOperand a = xs_slot(L.oSa, L.oSasc, m, n);       // columns of A
       const XsOperand bb = xs_slot(L.oSb, L.oSbsc, m, n);      // columns of B
@@ -1320,7 +1327,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       if ((r = xs_gemm(a, one ? a : bb, m, m, n, B.Cp.b0, map1(m), map1(1), L.per, gsplit, L.mm,
                        b.err, s)))
         return r;
-      k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, B.C, gsplit, m, 0, ns);
+      k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, out, gsplit, m, 0, ns);
       nl += one ? 3 : 4;
       return cudaGetLastError();
     }
@@ -1328,7 +1335,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       k_si_gram<float><<<dim3(L.NC, 1, P), 256, 0, s>>>(A, Bm, B.Cp, n, m, sym);
     else
       k_si_gram<double><<<dim3(L.NC, 1, P), 256, 0, s>>>(A, Bm, B.Cp, n, m, sym);
-    k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, B.C, L.NC, m, sym, ns);
+    k_si_gram_reduce<<<dim3(grid_1d(L.mm, P), 1, P), 256, 0, s>>>(B.Cp, out, L.NC, m, sym, ns);
     nl += 2;
     return cudaGetLastError();
   };
@@ -1361,7 +1368,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   };
   // one CholeskyQR pass with an FP32 factorisation: dst = src W
   auto cholqr32 = [&](PSet src, PSet dst, float sh) -> cudaError_t {
-    cudaError_t r = gram(src, src, true, true, false);
+    cudaError_t r = gram(src, src, true, true, false, B.C);
     if (r) return r;
     k_si_chol32<<<gz, kCholThreads, chol32_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
     nl += 1;
@@ -1369,16 +1376,11 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   };
   // one CholeskyQR pass in FP64 (robust for any conditioning with the shift)
   auto cholqr64 = [&](PSet src, PSet dst, double sh) -> cudaError_t {
-    cudaError_t r = gram(src, src, true, false, false);
+    cudaError_t r = gram(src, src, true, false, false, B.C);
     if (r) return r;
     k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
     nl += 1;
     return rot(src, B.W, dst, 1);
-  };
-  // FP64 Newton-Schulz step towards orthonormality: dst = src (3I - src^T src) / 2
-  auto polish = [&](PSet src, PSet dst) -> cudaError_t {
-    cudaError_t r = gram(src, src, true, false, true);
-    return r ? r : rot(src, B.C, dst, 0);
   };
   // dst = orth(src) through tmp (src is overwritten).  After the first
   // Rayleigh-Ritz step the basis holds Ritz vectors, G X is X Theta up to the
@@ -1442,19 +1444,40 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   double prev_worst = INFINITY;
   while (it < max_iter) {
     const bool check = (it + 1 >= next_check) || (it + 1 == max_iter);
-    if (check) {                    // the Rayleigh-Ritz step needs an FP64-orthonormal basis
-      // an FP64 CholeskyQR pass (any conditioning the shift allows) and one
-      // Newton-Schulz step: orthonormal to FP64 accuracy
-      if ((e = cholqr64(X, Z, shift)) || (e = polish(Z, X))) return e;
-    }
     if ((e = gemm(X, Y))) return e;  // Y = G X
     ++it;
     if (check) {
-      if ((e = gram(X, Y, false, false, false))) return e;   // H = X^T G X
-      if ((e = small_eig())) return e;                         // H = W Theta W^T
-      if ((e = rot(X, B.W, Z, 0))) return e;
+      // Rayleigh-Ritz on the span of X, whose columns the FP32 CholeskyQR left
+      // orthonormal only to about its own accuracy: with C0 = X^T X and
+      // W = C0^(-1/2) (Newton-Schulz on the m x m side, from C0 ~ I), X W is
+      // orthonormal to FP64 accuracy, G X W = Y W, and the projected matrix
+      // is H = W^T (X^T Y) W.  Its eigenvectors Z give the Ritz vectors X (W Z)
+      // and G X (W Z) = Y (W Z) with one rotation each.
+      auto slot = [&](int i) { return PSet{B.Cp.b0 + i * L.mm, B.Cp.b1 + i * L.mm, B.Cp.stride}; };
+      const PSet Wn = slot(3), Tn = slot(4), Ck = slot(5), Rr = slot(6);
+      const dim3 gmm((m + 7) / 8, (m + 7) / 8, P), g1(grid_1d(L.mm, P), 1, P);
+      if ((e = gram(X, X, true, false, false, B.W))) return e;   // C0 (B.W until small_eig)
+      if ((e = gram(X, Y, false, false, false, B.C))) return e;  // X^T Y
+      k_rr_axpi<<<g1, 256, 0, s>>>(B.W, -0.5, 1.5, Wn, m);       // W1 = (3I - C0) / 2
+      nl += 1;
+      for (int ns = 0; ns < 3; ++ns) {                              // W <- W (3I - W^T C0 W) / 2
+        k_rr_mm<<<gmm, 256, 0, s>>>(B.W, 0, Wn, 1.0, 0.0, Tn, m);   // C0 W
+        k_rr_mm<<<gmm, 256, 0, s>>>(Wn, 1, Tn, 1.0, 0.0, Ck, m);    // W^T C0 W
+        k_rr_mm<<<gmm, 256, 0, s>>>(Wn, 0, Ck, -0.5, 1.5, Tn, m);   // next W
+        k_si_copy<<<g1, 256, 0, s>>>(Tn, Wn, L.mm);
+        nl += 4;
+      }
+      k_rr_mm<<<gmm, 256, 0, s>>>(B.C, 0, Wn, 1.0, 0.0, Tn, m);     // (X^T Y) W
+      k_rr_mm<<<gmm, 256, 0, s>>>(Wn, 1, Tn, 1.0, 0.0, Ck, m);      // H = W^T X^T Y W
+      k_si_copy<<<g1, 256, 0, s>>>(Ck, B.C, L.mm);
+      nl += 3;
+      if ((e = cudaGetLastError())) return e;
+      if ((e = small_eig())) return e;                              // H = Z Theta Z^T (Z in B.W)
+      k_rr_mm<<<gmm, 256, 0, s>>>(Wn, 0, B.W, 1.0, 0.0, Rr, m);     // R = W Z
+      nl += 1;
+      if ((e = rot(X, Rr, Z, 0))) return e;
       std::swap(X, Z);
-      if ((e = rot(Y, B.W, Z, 0))) return e;
+      if ((e = rot(Y, Rr, Z, 0))) return e;
       std::swap(Y, Z);
       k_si_residual<<<dim3(k, 1, P), 256, 0, s>>>(X, Y, B.th, B.res, B.sig, b.has_trace ? 1 : 0, n, k);
       nl += 2;

@@ -128,6 +128,63 @@ __global__ void __launch_bounds__(256) k_xs_split(PSet src, int R, int K, IdxMap
   }
 }
 
+// The same slicing with one 256-thread block per row, for long rows (K >= 256):
+// the warp-per-row kernel leaves most of the GPU idle when there are few rows
+// (the n-long columns of a basis: 2m rows) and walks each row serially.  Same
+// arithmetic per element, so the slices are identical.
+template <int S>
+__global__ void __launch_bounds__(256) k_xs_split_row(PSet src, int R, int K, IdxMap rm, IdxMap km,
+                                                      __nv_bfloat16 *dst, int pitch, long long bstride,
+                                                      double *scale, long long sstride, PSet kscale,
+                                                      int kmode) {
+  const int z = blockIdx.z, r = blockIdx.x;
+  const double *a = src.at(z);
+  const double *ks = kmode ? kscale.at(z) : nullptr;
+  const long long ro = map_off(rm, r);
+  auto elem = [&](int k) {
+    const double v = a[ro + map_off(km, k)];
+    if (kmode == 1) return v * ks[k];
+    if (kmode == 2) return v / ks[k];
+    return v;
+  };
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  unsigned long long mb = 0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(elem(k))) & kAbs;
+    if (u > kInf) u = kInf;
+    mb = u > mb ? u : mb;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = t > mb ? t : mb;
+  }
+  __shared__ unsigned long long part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  mb = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) mb = part[w] > mb ? part[w] : mb;
+  const double mx = __longlong_as_double(static_cast<long long>(mb));
+  int e = 0;
+  const bool finite = mb < kInf;
+  if (finite && mb != 0) (void)frexp(mx, &e);
+  if (threadIdx.x == 0) scale[z * sstride + r] = finite ? ldexp(1.0, e) : NAN;
+  const double up = ldexp(1.0, kXsBits * S - e);
+  __nv_bfloat16 *out = dst + z * bstride + (long long)r * pitch;
+  const long long plane = (long long)R * pitch;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    long long N = finite ? __double2ll_rn(elem(k) * up) : 0;
+#pragma unroll
+    for (int p = S - 1; p >= 1; --p) {
+      const long long d = ((N + 32) & 63) - 32;
+      N = (N - d) >> kXsBits;
+      out[p * plane + k] = __float2bfloat16_rn(ldexpf((float)d, -kXsBits * (p + 1)));
+    }
+    out[k] = __float2bfloat16_rn(ldexpf((float)N, -kXsBits));
+  }
+}
+
 // The same slicing for operands whose rows are contiguous but whose K index is
 // strided (the basis of a rotation X W, column-major X as the A operand): a
 // block stages 32 rows x K (K <= kXsStagedK) through shared memory with loads
@@ -445,6 +502,20 @@ cudaError_t xs_split_scaled(PSet src, IdxMap rm, IdxMap km, PSet kscale, int kmo
       XS_STAGED_CASE(1) XS_STAGED_CASE(2) XS_STAGED_CASE(3) XS_STAGED_CASE(4)
       XS_STAGED_CASE(5) XS_STAGED_CASE(6) XS_STAGED_CASE(7) XS_STAGED_CASE(8)
 #undef XS_STAGED_CASE
+    }
+    return cudaGetLastError();
+  }
+  if (d.K >= 256) {
+    const dim3 gr(d.rows, 1, d.batch < 1 ? 1 : d.batch);
+    switch (d.S) {
+#define XS_ROW_CASE(SS)                                                                       \
+  case SS:                                                                                    \
+    k_xs_split_row<SS><<<gr, 256, 0, s>>>(src, d.rows, d.K, rm, km, dst, d.pitch, d.bstride,  \
+                                          d.scale, d.sstride, kscale, kmode);                 \
+    break;
+      XS_ROW_CASE(1) XS_ROW_CASE(2) XS_ROW_CASE(3) XS_ROW_CASE(4)
+      XS_ROW_CASE(5) XS_ROW_CASE(6) XS_ROW_CASE(7) XS_ROW_CASE(8)
+#undef XS_ROW_CASE
     }
     return cudaGetLastError();
   }
