@@ -475,7 +475,9 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
 // W = diag(d) R^-1 (column-major) such that Y W is orthonormal:
 //   C_hat = diag(d) C diag(d) + shift I = R^T R,  d_j = 1 / sqrt(C_jj).
 __global__ void __launch_bounds__(kCholThreads) k_si_chol(PSet Cin, int m, double shift, PSet Wout,
-                                                          int *flag) {
+                                                          int *flag, PSet only_if) {
+  // only_if (optional): run for problem z only if only_if.at(z)[2] != 0
+  if (only_if.b0 && only_if.at(blockIdx.z)[2] == 0.0) return;
   extern __shared__ double sh[];
   const int ld = m + 1;
   double *C = sh;                 // m x ld, upper triangle -> R
@@ -601,7 +603,7 @@ __device__ inline void jacobi_angle(double hpp, double hqq, double hpq, double &
 }
 
 __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout, PSet theta, int *flag,
-                                                   int *sweeps, int floor_exp) {
+                                                   int *sweeps, int floor_exp, int sig_exp) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int z = blockIdx.z;
@@ -626,7 +628,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
   int *aq = ap + 2 * half;                                  // q of every slot, same
   __shared__ int rotated;
   __shared__ unsigned int maxrel_bits;
-  __shared__ double s_floor;
+  __shared__ double s_floor, s_sig;
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
 
@@ -656,7 +658,13 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
     double v = 0.0;
     for (int i = threadIdx.x; i < m; i += 32) v = fmax(v, fabs(Cin.at(z)[(size_t)i * m + i]));
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) s_floor = ldexp(v, -floor_exp);
+    if (threadIdx.x == 0) {
+      s_floor = ldexp(v, -floor_exp);
+      // rotations below 2^-sig_exp of the largest diagonal entry do not hold
+      // the sweeps back (their entries are absolutely negligible, whatever
+      // their size against their own diagonal pair)
+      s_sig = ldexp(v, -sig_exp);
+    }
   }
   __syncthreads();
   // the round-0 inputs are read locally; remote writes only target buffer 1
@@ -689,7 +697,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
         if (fabs(hpq) > s_floor && hpq * hpq > 1e-30 * fabs(hpp * hqq) && fabs(hpq) > 1e-300) {
           const float den = fabsf((float)hpp * (float)hqq);
           const float rel2 = den > 0.0f ? fminf(1.0f, (float)hpq * (float)hpq / den) : 1.0f;
-          atomicMax(&maxrel_bits, __float_as_uint(rel2));
+          if (fabs(hpq) > s_sig) atomicMax(&maxrel_bits, __float_as_uint(rel2));
           jacobi_angle(hpp, hqq, hpq, c, sv);
           rotated = 1;
         }
@@ -824,10 +832,11 @@ size_t j32_smem(int m) {
 // round-robin pair order (every pair meets once per sweep).  Vout (FP64,
 // column-major) receives the accumulated rotation V (columns in the order of
 // the final diagonal, unsorted).  A pair is rotated while |h_pq| exceeds both
-// 2^-22 of the largest diagonal entry and 1e-6 of sqrt|h_pp h_qq|: above the
-// rounding noise each FP32 rotation leaves (about 2^-24 of the matrix norm),
-// which would otherwise keep being rotated; the FP64 stage removes what is
-// left.  The sweeps stop when none was rotated; the count goes to *sweeps
+// 2^-30 of the largest diagonal entry and 1e-6 of sqrt|h_pp h_qq|: entries
+// between two small diagonal entries are resolved to FP32 relative accuracy
+// (once the couplings to the large ones are small, the rounding noise the
+// rotations leave in them is relative to their own size), so that the FP64
+// stage starts in its quadratic regime.  The sweeps stop when none was rotated; the count goes to *sweeps
 // (maximum over problems).
 __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m, PSet Vout, int *sweeps) {
   extern __shared__ float jsh[];
@@ -857,7 +866,7 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
-  const float floor_abs = 0x1.0p-22f;      // the scaled largest diagonal entry lies in [1, 2)
+  const float floor_abs = 0x1.0p-30f;      // the scaled largest diagonal entry lies in [1, 2)
   int sweep = 0;
   for (; sweep < kJ32MaxSweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
@@ -917,6 +926,26 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int c = e / m, j = e % m;            // out[j + c m] = V[j][c]
     out[e] = (double)V[j * ld + c];
+  }
+}
+
+// flags.at(z)[2] = 1 if max |C_ij - delta_ij| > 1/4 (the Newton-Schulz
+// iteration for C^-1/2 from I is then not to be trusted), else 0.
+__global__ void k_rr_far_from_identity(PSet C, int m, PSet flags) {
+  const int z = blockIdx.z;
+  double v = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const double d = C.at(z)[e] - ((e % m == e / m) ? 1.0 : 0.0);
+    v = fmax(v, (d == d) ? fabs(d) : INFINITY);
+  }
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double w = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) w = fmax(w, part[i]);
+    flags.at(z)[2] = (w > 0.25) ? 1.0 : 0.0;
   }
 }
 
@@ -1163,7 +1192,7 @@ int grid_1d(long long count, int P) {
 }
 
 cudaError_t launch_jacobi(PSet C, int m, PSet W, PSet theta, int *flag, int *sweeps, int P,
-                          cudaStream_t s, int floor_exp = 56) {
+                          cudaStream_t s, int floor_exp = 56, int sig_exp = 2000) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(kCluster, 1, P);
   cfg.blockDim = dim3(512, 1, 1);
@@ -1176,7 +1205,7 @@ cudaError_t launch_jacobi(PSet C, int m, PSet W, PSet theta, int *flag, int *swe
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_si_jacobi, C, m, W, theta, flag, sweeps, floor_exp);
+  return cudaLaunchKernelEx(&cfg, k_si_jacobi, C, m, W, theta, flag, sweeps, floor_exp, sig_exp);
 }
 
 }  // namespace
@@ -1247,7 +1276,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     gs = XsOperand{work + L.oGs, work + L.oGsc, n, n, L.xsp, kSiSlices, P, L.per * 4, L.per};
     const int tiles = ((n + 127) / 128) * ((m + 95) / 96) * P;
     xsplit = std::max(xs_min_split(n), std::min(kSplitMax, (2 * 152 + tiles - 1) / tiles));
-    while (xsplit > xs_min_split(n) && (n + xsplit - 1) / xsplit < 256) --xsplit;
+    while (xsplit > xs_min_split(n) && (n + xsplit - 1) / xsplit < 128) --xsplit;
     const int gtiles = ((m + 79) / 80) * P;
     gsplit = std::max(xs_min_split(n), std::min(std::min(kChunkMax, n / 64), (2 * 152 + gtiles - 1) / gtiles));
     if ((e = xs_split(b.G, map1(n), map1(1), gs, s))) return e;
@@ -1360,8 +1389,10 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     // H' comes from two FP64 products: its entries carry rounding noise of
     // about m u ||H|| (2^-46 at m = 72), so entries below 2^-44 of its largest
     // diagonal entry are left alone (their effect on a residual is below
-    // 1e-13 of the largest eigenvalue)
-    if ((r = launch_jacobi(V2, m, T1, B.th, B.flag, B.sweeps, P, s, 44))) return r;   // T1 = W'
+    // 1e-13 of the largest eigenvalue), and a sweep whose rotated entries all
+    // lay below 2^-42 of it (2.3e-13 of the largest Ritz value: already within
+    // the residual bound) ends the iteration
+    if ((r = launch_jacobi(V2, m, T1, B.th, B.flag, B.sweeps, P, s, 44, 42))) return r;   // T1 = W'
     k_rr_mm<<<gmm, 256, 0, s>>>(V1, 0, T1, 1.0, 0.0, B.W, m);     // W = V1 W'
     nl += 2;
     return cudaGetLastError();
@@ -1378,7 +1409,7 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   auto cholqr64 = [&](PSet src, PSet dst, double sh) -> cudaError_t {
     cudaError_t r = gram(src, src, true, false, false, B.C);
     if (r) return r;
-    k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(B.C, m, sh, B.W, B.flag);
+    k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(B.C, m, sh, B.W, B.flag, PSet{nullptr, nullptr, 0});
     nl += 1;
     return rot(src, B.W, dst, 1);
   };
@@ -1467,6 +1498,12 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
         k_si_copy<<<g1, 256, 0, s>>>(Tn, Wn, L.mm);
         nl += 4;
       }
+      // where X is far from orthonormal (nearly dependent columns at a first
+      // check), W comes instead from a shifted FP64 Cholesky of C0 (X W is
+      // then orthonormal for any conditioning the shift allows)
+      k_rr_far_from_identity<<<gz, 256, 0, s>>>(B.W, m, B.sig);
+      k_si_chol<<<gz, kCholThreads, chol_smem(m), s>>>(B.W, m, shift, Wn, B.flag, B.sig);
+      nl += 2;
       k_rr_mm<<<gmm, 256, 0, s>>>(B.C, 0, Wn, 1.0, 0.0, Tn, m);     // (X^T Y) W
       k_rr_mm<<<gmm, 256, 0, s>>>(Wn, 1, Tn, 1.0, 0.0, Ck, m);      // H = W^T X^T Y W
       k_si_copy<<<g1, 256, 0, s>>>(Ck, B.C, L.mm);
