@@ -423,44 +423,65 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
     return;
   }
   // W = diag(d) R^-1.  Z = R^-1 (upper triangular, in the now free C storage)
-  // by panels of kCholPanel rows, the bottom panel first: for the panel's rows
-  // i and every column c >= i, t_ic = [i == c] - sum_{l past the panel, l <= c}
-  // R_il Z_lc (independent dot products, all threads), then each column solves
-  // the panel's small upper triangle R_II z = t (one thread per column).  Two
-  // barriers per panel instead of a dependent chain of length m per column.
+  // by 8 x 8 blocks: (1) every diagonal block Z_II = R_II^-1 by back
+  // substitution, one thread per column; (2) the off-diagonal blocks by
+  // distance d = J - I, all blocks of one distance at once:
+  // Z_IJ = -Z_II sum_{K = I+1..J} R_IK Z_KJ (the blocks Z_KJ, K > I, have
+  // smaller distances).  Two barriers per distance: the dependent chains are
+  // at most 8 d long instead of m.
+  constexpr int BS = kCholPanel;
+  const int nb = (m + BS - 1) / BS;
   float *Z = C;
-  float *rinv = d + m;                    // m: 1 / R_ii
-  float *Tp = rinv + m;                   // kCholPanel x m: right-hand sides of a panel
-  for (int i = threadIdx.x; i < m; i += blockDim.x) rinv[i] = 1.0f / R[i * ld + i];
+  float *Tt = d + m;                      // nb BS x BS scratch blocks: the sums of one distance
+  for (int e = threadIdx.x; e < m * ld; e += blockDim.x) Z[e] = 0.0f;
   __syncthreads();
-  const int last = ((m - 1) / kCholPanel) * kCholPanel;
-  for (int i0 = last; i0 >= 0; i0 -= kCholPanel) {
-    const int w = min(kCholPanel, m - i0), cols = m - i0;
-    for (int e = threadIdx.x; e < w * cols; e += blockDim.x) {
-      const int ii = e / cols, c = i0 + e % cols, i = i0 + ii;
-      float acc = (i == c) ? 1.0f : 0.0f;
-      for (int l = i0 + w; l <= c; ++l) acc = fmaf(-R[i * ld + l], Z[l * ld + c], acc);
-      Tp[ii * m + c] = acc;
-    }
-    __syncthreads();
-    for (int c = i0 + threadIdx.x; c < m; c += blockDim.x) {
-      float zc[kCholPanel];
+  for (int t = threadIdx.x; t < nb * BS; t += blockDim.x) {
+    const int I = t / BS, cl = t % BS, i0 = I * BS, w = min(BS, m - i0);
+    if (cl < w) {
+      const int c = i0 + cl;
+      float zc[BS];
 #pragma unroll
-      for (int ii = kCholPanel - 1; ii >= 0; --ii) {
-        const int i = i0 + ii;
+      for (int ii = BS - 1; ii >= 0; --ii) {
         float v = 0.0f;
-        if (ii < w && i <= c) {
-          v = Tp[ii * m + c];
+        if (ii <= cl) {
+          const int i = i0 + ii;
+          v = (ii == cl) ? 1.0f : 0.0f;
 #pragma unroll
-          for (int kk = ii + 1; kk < kCholPanel; ++kk)
-            if (kk < w) v = fmaf(-R[i * ld + i0 + kk], zc[kk], v);
-          v *= rinv[i];
+          for (int kk = ii + 1; kk < BS; ++kk)
+            if (kk <= cl) v = fmaf(-R[i * ld + i0 + kk], zc[kk], v);
+          v /= R[i * ld + i];
         }
         zc[ii] = v;
       }
 #pragma unroll
-      for (int ii = 0; ii < kCholPanel; ++ii)
-        if (ii < w) Z[(i0 + ii) * ld + c] = zc[ii];
+      for (int ii = 0; ii < BS; ++ii)
+        if (ii <= cl) Z[(i0 + ii) * ld + c] = zc[ii];
+    }
+  }
+  __syncthreads();
+  for (int dist = 1; dist < nb; ++dist) {
+    const int nblk = nb - dist;
+    // T_IJ[i][j] = sum_{k in blocks I+1..J} R[i][k] Z[k][j]
+    for (int t = threadIdx.x; t < nblk * BS * BS; t += blockDim.x) {
+      const int I = t / (BS * BS), ij = t % (BS * BS), ii = ij / BS, jj = ij % BS;
+      const int J = I + dist, i = I * BS + ii, j = J * BS + jj;
+      float v = 0.0f;
+      if (i < m && j < m) {
+        const int k1 = min(m, J * BS + BS);
+        for (int k = (I + 1) * BS; k < k1; ++k) v = fmaf(R[i * ld + k], Z[k * ld + j], v);
+      }
+      Tt[t] = v;
+    }
+    __syncthreads();
+    // Z_IJ = -Z_II T_IJ
+    for (int t = threadIdx.x; t < nblk * BS * BS; t += blockDim.x) {
+      const int I = t / (BS * BS), ij = t % (BS * BS), ii = ij / BS, jj = ij % BS;
+      const int J = I + dist, i0 = I * BS, i = i0 + ii, j = J * BS + jj;
+      if (i < m && j < m) {
+        float v = 0.0f;
+        for (int l = ii; l < BS && i0 + l < m; ++l) v = fmaf(Z[i * ld + i0 + l], Tt[I * BS * BS + l * BS + jj], v);
+        Z[i * ld + j] = -v;
+      }
     }
     __syncthreads();
   }
@@ -825,7 +846,10 @@ constexpr int kJ32Threads = 1024;
 constexpr int kJ32MaxSweeps = 30;
 
 size_t j32_smem(int m) {
-  return (size_t)(2 * m * (m + 1) + 2 * (m / 2)) * sizeof(float) + (size_t)(2 * (m / 2)) * sizeof(int);
+  const int half = m / 2;
+  return (size_t)(2 * m * (m + 1)) * sizeof(float) +              // A, V
+         (size_t)(kJ32Threads / 32) * 2 * half * sizeof(float) +  // per-warp (c, s) tables
+         (size_t)2 * 3 * half * sizeof(float);                      // angle inputs, by round parity
 }
 
 // FP32 cyclic Jacobi on the symmetric m x m matrix C of problem z (m even),
@@ -836,17 +860,22 @@ size_t j32_smem(int m) {
 // between two small diagonal entries are resolved to FP32 relative accuracy
 // (once the couplings to the large ones are small, the rounding noise the
 // rotations leave in them is relative to their own size), so that the FP64
-// stage starts in its quadratic regime.  The sweeps stop when none was rotated; the count goes to *sweeps
-// (maximum over problems).
+// stage starts in its quadratic regime.  The sweeps stop when none was
+// rotated; the count goes to *sweeps (maximum over problems).
+//
+// One barrier per round: every warp computes the angles of all pairs of the
+// round itself, from a table of the pairs' 2 x 2 diagonal blocks that the
+// previous round published (double-buffered by round parity), then applies
+// its share of the rotations (Eq. 6 per 2 x 2 block of rows and columns) and
+// publishes the entries that form the next round's blocks.
 __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m, PSet Vout, int *sweeps) {
   extern __shared__ float jsh[];
   const int ld = m + 1, half = m / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *A = jsh;
   float *V = A + m * ld;
-  float *cs = V + m * ld;
-  float *sn = cs + half;
-  int *pp = reinterpret_cast<int *>(sn + half);
-  int *qq = pp + half;
+  float *wtab = V + m * ld + warp * 2 * half;       // this warp's c[half], s[half]
+  float *nd = V + m * ld + (kJ32Threads / 32) * 2 * half;   // [parity][slot][h_top, h_bot, h_pq]
   __shared__ double s_scale;
   __shared__ int s_rot;
   const int z = blockIdx.z;
@@ -866,35 +895,53 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
+  // slot and side (0 top, 1 bottom) of index x in round rr
+  auto where = [&](int x, int rr, int &sl, int &tb) {
+    if (x == 0) { sl = 0; tb = 0; return; }
+    const int c = ((x - 1 - rr) % (m - 1) + (m - 1)) % (m - 1);   // circle position
+    if (c <= half - 2) { sl = c + 1; tb = 0; } else { sl = m - 2 - c; tb = 1; }
+  };
+  __syncthreads();
+  for (int sl = threadIdx.x; sl < half; sl += blockDim.x) {
+    const int u = top_index(sl, 0), v = bot_index(sl, 0);
+    nd[sl * 3 + 0] = A[u * ld + u];
+    nd[sl * 3 + 1] = A[v * ld + v];
+    nd[sl * 3 + 2] = A[min(u, v) * ld + max(u, v)];
+  }
   const float floor_abs = 0x1.0p-30f;      // the scaled largest diagonal entry lies in [1, 2)
-  int sweep = 0;
+  int sweep = 0, rg = 0;                   // rg: rounds so far (parity of the input table)
   for (; sweep < kJ32MaxSweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
-    for (int r = 0; r < m - 1; ++r) {
-      for (int k = threadIdx.x; k < half; k += blockDim.x) {
+    for (int r = 0; r < m - 1; ++r, ++rg) {
+      const float *ndc = nd + (rg & 1) * 3 * half;
+      float *ndn = nd + ((rg + 1) & 1) * 3 * half;
+      const int rn = (r + 1) % (m - 1);
+      // (1) every warp: the angles of all pairs of this round
+      for (int k = lane; k < half; k += 32) {
         const int u = top_index(k, r), v = bot_index(k, r);
-        const int p = min(u, v), q = max(u, v);
-        const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+        const float app = (u < v) ? ndc[k * 3 + 0] : ndc[k * 3 + 1];
+        const float aqq = (u < v) ? ndc[k * 3 + 1] : ndc[k * 3 + 0];
+        const float apq = ndc[k * 3 + 2];
         float c = 1.0f, sv = 0.0f;
         if (fabsf(apq) > floor_abs && apq * apq > 1e-12f * fabsf(app * aqq)) {
           const float tau = (aqq - app) / (2.0f * apq);
           const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
           c = rsqrtf(fmaf(t, t, 1.0f));
           sv = t * c;
-          s_rot = 1;
+          if (warp == 0) s_rot = 1;
         }
-        cs[k] = c;
-        sn[k] = sv;
-        pp[k] = p;
-        qq[k] = q;
+        wtab[k] = c;
+        wtab[half + k] = sv;
       }
-      __syncthreads();
-      // M'_IJ = J_I^T M_IJ J_J for every 2 x 2 block (the blocks are disjoint)
+      __syncwarp();
+      // (2) M'_IJ = J_I^T M_IJ J_J for this thread's 2 x 2 blocks; entries that
+      // form a pair of the next round go to its angle-input table
       for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
         const int I = e / half, J = e % half;
-        const int pI = pp[I], qI = qq[I], pJ = pp[J], qJ = qq[J];
-        const float cI = cs[I], sI = sn[I], cJ = cs[J], sJ = sn[J];
+        const int uI = top_index(I, r), vI = bot_index(I, r), uJ = top_index(J, r), vJ = bot_index(J, r);
+        const int pI = min(uI, vI), qI = max(uI, vI), pJ = min(uJ, vJ), qJ = max(uJ, vJ);
+        const float cI = wtab[I], sI = wtab[half + I], cJ = wtab[J], sJ = wtab[half + J];
         const float a00 = A[pI * ld + pJ], a01 = A[pI * ld + qJ];
         const float a10 = A[qI * ld + pJ], a11 = A[qI * ld + qJ];
         const float b00 = cJ * a00 - sJ * a01, b01 = sJ * a00 + cJ * a01;
@@ -906,14 +953,29 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
         A[pI * ld + qJ] = n01;
         A[qI * ld + pJ] = n10;
         A[qI * ld + qJ] = n11;
+        const int ri[4] = {pI, pI, qI, qI}, cj[4] = {pJ, qJ, pJ, qJ};
+        const float vals[4] = {n00, n01, n10, n11};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int i = ri[h], j = cj[h];
+          if (i > j) continue;                     // each pair's entry once, from the upper triangle
+          int si, ti, sj, tj;
+          where(i, rn, si, ti);
+          where(j, rn, sj, tj);
+          if (si != sj) continue;
+          if (i == j) ndn[si * 3 + ti] = vals[h];
+          else ndn[si * 3 + 2] = vals[h];
+        }
       }
       // V <- V J
       for (int e = threadIdx.x; e < m * half; e += blockDim.x) {
         const int row = e / half, J = e % half;
-        const int pJ = pp[J], qJ = qq[J];
+        const int uJ = top_index(J, r), vJ = bot_index(J, r);
+        const int pJ = min(uJ, vJ), qJ = max(uJ, vJ);
+        const float cJ = wtab[J], sJ = wtab[half + J];
         const float x = V[row * ld + pJ], y = V[row * ld + qJ];
-        V[row * ld + pJ] = cs[J] * x - sn[J] * y;
-        V[row * ld + qJ] = sn[J] * x + cs[J] * y;
+        V[row * ld + pJ] = cJ * x - sJ * y;
+        V[row * ld + qJ] = sJ * x + cJ * y;
       }
       __syncthreads();
     }
@@ -1170,7 +1232,10 @@ size_t jacobi_smem(int m) {
          (size_t)(4 * half) * sizeof(int) + 64;
 }
 size_t chol_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m) * sizeof(double); }
-size_t chol32_smem(int m) { return (size_t)(2 * m * (m + 1) + 2 * m + kCholPanel * m) * sizeof(float); }
+size_t chol32_smem(int m) {
+  const int nb = (m + kCholPanel - 1) / kCholPanel;
+  return (size_t)(2 * m * (m + 1) + m + nb * kCholPanel * kCholPanel) * sizeof(float);
+}
 
 cudaError_t set_attrs() {
   static bool done = false;
