@@ -846,10 +846,7 @@ constexpr int kJ32Threads = 1024;
 constexpr int kJ32MaxSweeps = 30;
 
 size_t j32_smem(int m) {
-  const int half = m / 2;
-  return (size_t)(2 * m * (m + 1)) * sizeof(float) +              // A, V
-         (size_t)(kJ32Threads / 32) * 2 * half * sizeof(float) +  // per-warp (c, s) tables
-         (size_t)2 * 3 * half * sizeof(float);                      // angle inputs, by round parity
+  return (size_t)(2 * m * (m + 1) + 2 * (m / 2)) * sizeof(float) + (size_t)(2 * (m / 2)) * sizeof(int);
 }
 
 // FP32 cyclic Jacobi on the symmetric m x m matrix C of problem z (m even),
@@ -860,22 +857,17 @@ size_t j32_smem(int m) {
 // between two small diagonal entries are resolved to FP32 relative accuracy
 // (once the couplings to the large ones are small, the rounding noise the
 // rotations leave in them is relative to their own size), so that the FP64
-// stage starts in its quadratic regime.  The sweeps stop when none was
-// rotated; the count goes to *sweeps (maximum over problems).
-//
-// One barrier per round: every warp computes the angles of all pairs of the
-// round itself, from a table of the pairs' 2 x 2 diagonal blocks that the
-// previous round published (double-buffered by round parity), then applies
-// its share of the rotations (Eq. 6 per 2 x 2 block of rows and columns) and
-// publishes the entries that form the next round's blocks.
+// stage starts in its quadratic regime.  The sweeps stop when none was rotated; the count goes to *sweeps
+// (maximum over problems).
 __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m, PSet Vout, int *sweeps) {
   extern __shared__ float jsh[];
   const int ld = m + 1, half = m / 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *A = jsh;
   float *V = A + m * ld;
-  float *wtab = V + m * ld + warp * 2 * half;       // this warp's c[half], s[half]
-  float *nd = V + m * ld + (kJ32Threads / 32) * 2 * half;   // [parity][slot][h_top, h_bot, h_pq]
+  float *cs = V + m * ld;
+  float *sn = cs + half;
+  int *pp = reinterpret_cast<int *>(sn + half);
+  int *qq = pp + half;
   __shared__ double s_scale;
   __shared__ int s_rot;
   const int z = blockIdx.z;
@@ -895,53 +887,35 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
-  // slot and side (0 top, 1 bottom) of index x in round rr
-  auto where = [&](int x, int rr, int &sl, int &tb) {
-    if (x == 0) { sl = 0; tb = 0; return; }
-    const int c = ((x - 1 - rr) % (m - 1) + (m - 1)) % (m - 1);   // circle position
-    if (c <= half - 2) { sl = c + 1; tb = 0; } else { sl = m - 2 - c; tb = 1; }
-  };
-  __syncthreads();
-  for (int sl = threadIdx.x; sl < half; sl += blockDim.x) {
-    const int u = top_index(sl, 0), v = bot_index(sl, 0);
-    nd[sl * 3 + 0] = A[u * ld + u];
-    nd[sl * 3 + 1] = A[v * ld + v];
-    nd[sl * 3 + 2] = A[min(u, v) * ld + max(u, v)];
-  }
   const float floor_abs = 0x1.0p-30f;      // the scaled largest diagonal entry lies in [1, 2)
-  int sweep = 0, rg = 0;                   // rg: rounds so far (parity of the input table)
+  int sweep = 0;
   for (; sweep < kJ32MaxSweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
-    for (int r = 0; r < m - 1; ++r, ++rg) {
-      const float *ndc = nd + (rg & 1) * 3 * half;
-      float *ndn = nd + ((rg + 1) & 1) * 3 * half;
-      const int rn = (r + 1) % (m - 1);
-      // (1) every warp: the angles of all pairs of this round
-      for (int k = lane; k < half; k += 32) {
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = threadIdx.x; k < half; k += blockDim.x) {
         const int u = top_index(k, r), v = bot_index(k, r);
-        const float app = (u < v) ? ndc[k * 3 + 0] : ndc[k * 3 + 1];
-        const float aqq = (u < v) ? ndc[k * 3 + 1] : ndc[k * 3 + 0];
-        const float apq = ndc[k * 3 + 2];
+        const int p = min(u, v), q = max(u, v);
+        const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
         float c = 1.0f, sv = 0.0f;
         if (fabsf(apq) > floor_abs && apq * apq > 1e-12f * fabsf(app * aqq)) {
           const float tau = (aqq - app) / (2.0f * apq);
           const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
           c = rsqrtf(fmaf(t, t, 1.0f));
           sv = t * c;
-          if (warp == 0) s_rot = 1;
+          s_rot = 1;
         }
-        wtab[k] = c;
-        wtab[half + k] = sv;
+        cs[k] = c;
+        sn[k] = sv;
+        pp[k] = p;
+        qq[k] = q;
       }
-      __syncwarp();
-      // (2) M'_IJ = J_I^T M_IJ J_J for this thread's 2 x 2 blocks; entries that
-      // form a pair of the next round go to its angle-input table
+      __syncthreads();
+      // M'_IJ = J_I^T M_IJ J_J for every 2 x 2 block (the blocks are disjoint)
       for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
         const int I = e / half, J = e % half;
-        const int uI = top_index(I, r), vI = bot_index(I, r), uJ = top_index(J, r), vJ = bot_index(J, r);
-        const int pI = min(uI, vI), qI = max(uI, vI), pJ = min(uJ, vJ), qJ = max(uJ, vJ);
-        const float cI = wtab[I], sI = wtab[half + I], cJ = wtab[J], sJ = wtab[half + J];
+        const int pI = pp[I], qI = qq[I], pJ = pp[J], qJ = qq[J];
+        const float cI = cs[I], sI = sn[I], cJ = cs[J], sJ = sn[J];
         const float a00 = A[pI * ld + pJ], a01 = A[pI * ld + qJ];
         const float a10 = A[qI * ld + pJ], a11 = A[qI * ld + qJ];
         const float b00 = cJ * a00 - sJ * a01, b01 = sJ * a00 + cJ * a01;
@@ -953,29 +927,14 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
         A[pI * ld + qJ] = n01;
         A[qI * ld + pJ] = n10;
         A[qI * ld + qJ] = n11;
-        const int ri[4] = {pI, pI, qI, qI}, cj[4] = {pJ, qJ, pJ, qJ};
-        const float vals[4] = {n00, n01, n10, n11};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int i = ri[h], j = cj[h];
-          if (i > j) continue;                     // each pair's entry once, from the upper triangle
-          int si, ti, sj, tj;
-          where(i, rn, si, ti);
-          where(j, rn, sj, tj);
-          if (si != sj) continue;
-          if (i == j) ndn[si * 3 + ti] = vals[h];
-          else ndn[si * 3 + 2] = vals[h];
-        }
       }
       // V <- V J
       for (int e = threadIdx.x; e < m * half; e += blockDim.x) {
         const int row = e / half, J = e % half;
-        const int uJ = top_index(J, r), vJ = bot_index(J, r);
-        const int pJ = min(uJ, vJ), qJ = max(uJ, vJ);
-        const float cJ = wtab[J], sJ = wtab[half + J];
+        const int pJ = pp[J], qJ = qq[J];
         const float x = V[row * ld + pJ], y = V[row * ld + qJ];
-        V[row * ld + pJ] = cJ * x - sJ * y;
-        V[row * ld + qJ] = sJ * x + cJ * y;
+        V[row * ld + pJ] = cs[J] * x - sn[J] * y;
+        V[row * ld + qJ] = sn[J] * x + cs[J] * y;
       }
       __syncthreads();
     }
