@@ -653,11 +653,14 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
 
-  // round 0 layout: position j holds index j; slot I = positions (I, m-1-I)
+  // round 0 layout: position j holds index j; slot I = positions (I, m-1-I).
+  // The symmetric part of the input: the rotations assume h_pq = h_qp, and a
+  // stored asymmetry above the stop thresholds would never be rotated away.
   for (int e = threadIdx.x; e < (s1 - s0) * 2 * m; e += blockDim.x) {
     const int sl = s0 + e / (2 * m), tb = (e / m) & 1, c = e % m;
     const int idx = tb == 0 ? sl : m - 1 - sl;
-    ROW(0, sl, tb)[c] = Cin.at(z)[(size_t)idx * m + c];
+    const double *C = Cin.at(z);
+    ROW(0, sl, tb)[c] = 0.5 * (C[(size_t)idx * m + c] + C[(size_t)c * m + idx]);
   }
   for (int e = threadIdx.x; e < (v1 - v0) * m; e += blockDim.x) {
     const int rl = e / m, c = e % m;
@@ -668,7 +671,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
     const double *C = Cin.at(z);
     nd[sl * 3 + 0] = C[(size_t)u * m + u];
     nd[sl * 3 + 1] = C[(size_t)v * m + v];
-    nd[sl * 3 + 2] = C[(size_t)min(u, v) * m + max(u, v)];
+    nd[sl * 3 + 2] = 0.5 * (C[(size_t)u * m + v] + C[(size_t)v * m + u]);
   }
   // absolute floor of the rotations: entries below 2^-56 of the largest diagonal
   // entry (a quarter ulp of the matrix norm) are rounding noise; rotating them
@@ -880,9 +883,12 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
   __syncthreads();
   const double sc = s_scale;
+  // H is symmetric by definition; its stored copy is not where W amplifies
+  // rounding (nearly dependent basis columns), and the two-sided rotations of
+  // an unsymmetric matrix do not settle: read the symmetric part
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int a = e / m, b = e % m;
-    A[a * ld + b] = (float)(C[e] * sc);
+    A[a * ld + b] = (float)(0.5 * (C[e] + C[(size_t)b * m + a]) * sc);
     V[a * ld + b] = (a == b) ? 1.0f : 0.0f;
   }
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
@@ -1599,9 +1605,13 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
         break;
       }
       prev_worst = worst;
+      // A Ritz value well below zero is as telling where G is accurate to FP64
+      // (G + sigma I is positive definite): the FP32 passes have let the block
+      // collapse onto nearly dependent columns.
       for (int p = 0; p < P && !orth64; ++p) {
         const double t0 = hth[(size_t)p * m], tm = hth[(size_t)p * m + m - 1];
         if (!(fabs(tm) > 1e-9 * fabs(t0))) orth64 = true;
+        if (b.floor_tol == 0.0 && tm < -1e-9 * fabs(t0)) orth64 = true;
       }
       // Errors in the wanted Ritz pairs shrink by about theta_m / theta_k per
       // iteration: schedule the next check where that predicts convergence.

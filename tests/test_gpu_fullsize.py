@@ -98,7 +98,7 @@ def run_to_steady(pkg, cfg, prec):
 
 
 @pytest.mark.parametrize("name,prec", [("ising_044h_d48", "fp64"), ("ising_044_d32", "fp64"),
-                                       ("ising_044h_d48", "tf32")])
+                                       ("ising_044h_d48", "tf32"), ("ising_044_d32", "tf32")])
 def test_sampled_full_size_step(pkg, name, prec):
     cfg = CONFIGS[name]
     h, d = run_to_steady(pkg, cfg, prec)
@@ -198,8 +198,11 @@ def test_batched_sweep_subset_matches_single_contexts(pkg):
     environments, so an instance can take more subspace iterations than alone;
     where a TF32 environment has a flat noise tail (low-temperature instances)
     the solver accepts a residual at the noise floor of G (2 u) after 24
-    iterations, and the two runs then differ at that floor's second order,
-    far below the TF32 error itself (~2e-4): bounded here at 1e-6."""
+    iterations, and the two runs then differ at that floor's second order:
+    (2u)^2 = 9.5e-7 per leading Ritz value and step, summed over the steps
+    with the weights 2^-n of ln Z / N and over both environments (measured
+    up to 1.1e-6).  Bounded at 1e-5, about ten times (2u)^2 and still twenty
+    times below the TF32 error itself (~2e-4)."""
     models, _ = sweep_rows()
     T0s = [pkg.ising_tensor(m.beta, m.h) for m in models]
     with pkg.HotrgBatch(T0s, [m.D_cut for m in models], "tf32") as bt:
@@ -212,4 +215,4 @@ def test_batched_sweep_subset_matches_single_contexts(pkg):
         with pkg.Hotrg(T0s[i], D, "tf32") as one:
             one.run(models[i].steps)
             single = one.ln_z_per_site()
-        assert abs(lz[i] / single - 1) < 1e-6, (D, lz[i], single)
+        assert abs(lz[i] / single - 1) < 1e-5, (D, lz[i], single)
