@@ -43,6 +43,7 @@ SWEEP_METRIC = "HOTRG aggregate RG-steps/s, batched beta sweep (instance-steps/s
 EIG_NOTE = "fp64 batched subspace iteration + two-sided Jacobi Rayleigh-Ritz (top D'+1 pairs, both sides)"
 L2_FLUSH_BYTES = 512 << 20
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor throughput
+FUSED_D = (16, 32)                  # steady D_cut of TF32 runs that take the fused a6 + a7 kernel
 # BF16 tensor-core products per algorithmic product: split planes, or for the
 # exact-slice mode the 21 digit pairs (s + t <= 7) of six base-64 digits
 BF16_SPLIT_PRODUCTS = {"bf16x3": 3, "bf16x6": 6, "bf16xs": 21}
@@ -83,14 +84,15 @@ def peaks():
     return 1900.0, 1700.0, 6800.0, "fallback"
 
 
-def captured_traffic(workload, precision):
-    """DRAM bytes per a6 launch from a committed ncu summary, or None when the
-    summary is for another workload or the GEMM kernel source changed since."""
+def captured_traffic(workload, precision, fused=False):
+    """DRAM bytes per launch of the bond-contraction kernel (the fused a6 + a7
+    kernel, or the a6 GEMM) from a committed ncu summary, or None when the
+    summary is for another workload or the kernel source changed since."""
     import hashlib
     import glob
-    src = os.path.join(ROOT, "paper_2602_05900_gb300", "csrc", "tc_gemm.cu")
+    src = os.path.join(ROOT, "paper_2602_05900_gb300", "csrc", "tc_chain.cu" if fused else "tc_gemm.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    for path in glob.glob(os.path.join(ROOT, "profiles", "a6_*.md")):
+    for path in glob.glob(os.path.join(ROOT, "profiles", "chain_*.md" if fused else "a6_*.md")):
         fields = {}
         for line in open(path):
             if ":" in line and line.startswith("    "):
@@ -384,20 +386,31 @@ def run_ours(args, world, rank, local):
     value = world * args.steps / (max_ms / 1e3)
     bf16_burst, bf16_sust, hbm, peak_src = peaks()
 
-    # dominant contraction kernel: the bond contraction Q = P.T (a6), one launch per step
+    # dominant contraction kernel, one launch per step: the a6 GEMM Q = P.T (the
+    # fused a6 + a7 kernel is an option, off by default: see the fused_chain block)
+    fused = False
     q_ms = prof["ms"]["proj_q"] / max(1, prof["stage_launches"]["proj_q"])
-    q_flops = 2.0 * D ** 7
+    q_flops = 2.0 * D ** 7 + (2.0 * D ** 6 if fused else 0.0)
     achieved = q_flops / (q_ms / 1e3) / 1e12
     peak, peak_note = tensor_peak(prec, bf16_burst, peak_src, measured)
-    roofline = {"kernel": "k_tc_gemm a6 bond contraction Q=P.T" if prec != "fp64" else "k_gemm_f64 a6",
+    if fused:
+        kname = "k_tc_chain fused a6 + a7 (Q = P.T contracted with U on chip)"
+        alg_bytes = 4 * (D ** 5 + 2 * D ** 4) + 8 * D ** 4     # P, T view, U read; T' (FP64) written
+    else:
+        kname = "k_tc_gemm a6 bond contraction Q=P.T" if prec != "fp64" else "k_gemm_f64 a6"
+        alg_bytes = 4 * (D ** 5 + D ** 4 + D ** 5) if prec == "tf32" else None
+    roofline = {"kernel": kname,
                 "bound": "tensor" if prec != "fp64" else "alu", "achieved": round(achieved, 2),
                 "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": captured_traffic(cfg.name, prec), "traffic_unit": "bytes/launch",
-                "algorithmic_bytes": 4 * (D ** 5 + D ** 4 + D ** 5) if prec == "tf32" else None,
+                "traffic": captured_traffic(cfg.name, prec, fused), "traffic_unit": "bytes/launch",
+                "algorithmic_bytes": alg_bytes,
                 "peak_source": peak_note,
                 "frac_of_nominal_tf32_from_bf16": round(achieved / (bf16_burst * TF32_PER_BF16), 4)
                 if prec == "tf32" else None,
                 "flops_per_launch": q_flops, "ms_per_launch": round(q_ms, 5)}
+    if fused:
+        # Q's write (a6 epilogue) and read (a7 operand) that the fusion removes
+        roofline["q_round_trip_bytes_saved"] = 2 * 4 * D ** 5
 
     ms_step = max_ms / args.steps
     out = {"metric": METRIC, "value": round(value, 4), "unit": "RG-steps/s", "n_gpus": world,
@@ -450,12 +463,54 @@ def run_ours(args, world, rank, local):
             "note": "the plain FP64 GPU path against the FP64 oracle on the host cores (same arithmetic); "
                     "the headline value is TF32 contractions and is not a same-precision comparison"}
         out["fp64_grade"] = fp64_grade_block(pkg, stream, torch, flush, measured)
+        if prec == "tf32" and D in FUSED_D:
+            out["fused_chain"] = fused_chain_block(pkg, cfg, stream, torch, flush, measured)
         out["sweep"] = sweep_block(pkg, torch, flush, measured, bf16_burst, peak_src)
         out["precision_modes"] = precision_modes(pkg, stream, torch)
         out["quantum_chain"] = quantum_report(pkg, stream, torch, flush)
         out["itebd"] = itebd_report(pkg, torch)
         out["itebd"]["cpu_baseline"] = itebd_cpu_baseline()
     return out
+
+
+def fused_chain_block(pkg, cfg, stream, torch, flush, measured, steps=6):
+    """The fused a6 + a7 kernel (Q = P.T contracted with U on chip, never
+    written to device memory) against the two-GEMM chain on the same
+    steady-state steps: stage-profiler time of the bond contraction and
+    projection stages per step, and the device-memory bytes each moves."""
+    from paper_2602_05900_gb300.capi import OPT_FUSED_CHAIN
+    D = cfg.D_cut
+    res = {}
+    for fuse in (1, 0):
+        h, d = steady_job(pkg, cfg, "tf32", stream)
+        h.set_option(OPT_FUSED_CHAIN, fuse)
+        _, d = time_steps(torch, h, d, 2, stream, flush)
+        h.profile_enable(True)
+        times, d = time_steps(torch, h, d, steps, stream, flush)
+        prof = h.profile_read()
+        h.close()
+        n = max(1, prof["steps"])
+        res[fuse] = {"ms_per_step": sum(times) / len(times),
+                     "proj_q_ms": prof["ms"]["proj_q"] / n, "proj_t_ms": prof["ms"]["proj_t"] / n}
+    f, c = res[1], res[0]
+    flops = 2.0 * D ** 7 + 2.0 * D ** 6
+    tf32_peak = measured.get("tf32_tflops") if measured else None
+    fused_tf = flops / (f["proj_q_ms"] / 1e3) / 1e12
+    return {"workload": f"{cfg.name} tf32 steady state, {steps} steps each",
+            "fused_kernel_ms": round(f["proj_q_ms"], 4),
+            "two_gemm_chain_ms": round(c["proj_q_ms"] + c["proj_t_ms"], 4),
+            "two_gemm_a6_ms": round(c["proj_q_ms"], 4), "two_gemm_a7_ms": round(c["proj_t_ms"], 4),
+            "step_ms_fused": round(f["ms_per_step"], 4), "step_ms_two_gemm": round(c["ms_per_step"], 4),
+            "fused_achieved_tflops": round(fused_tf, 2),
+            "fused_frac_of_measured_tf32": round(fused_tf / tf32_peak, 4) if tf32_peak else None,
+            "algorithmic_bytes_fused": 4 * (D ** 5 + 2 * D ** 4) + 8 * D ** 4,
+            "algorithmic_bytes_two_gemm": 4 * (D ** 5 + D ** 4 + D ** 5) + 4 * (D ** 5 + D ** 4) + 8 * D ** 4,
+            "q_round_trip_bytes_saved": 2 * 4 * D ** 5,
+            "default": "two-GEMM chain (HOTRG_OPT_FUSED_CHAIN = 0)",
+            "note": "the fused kernel's second product has N = 16 (the (y, y') pairs of an a6 tile); "
+                    "on GB300 such MMAs hold the tensor pipe about as long as N = 128 ones, so the kernel "
+                    "issues twice the MMAs of a6 alone for 3 % more flops and is slower than the "
+                    "two-GEMM chain despite moving 268 MB less"}
 
 
 def fp64_grade_block(pkg, stream, torch, flush, measured):
@@ -503,14 +558,15 @@ def sweep_block(pkg, torch, flush, measured, bf16_burst, peak_src, steps=3):
     prof = bt.profile_read()
     bt.close()
     ms = sum(times)
-    q_flops = sum(2.0 * m.D_cut ** 7 for m in models)
+    q_flops = sum(2.0 * m.D_cut ** 7 + (2.0 * m.D_cut ** 6 if m.D_cut in FUSED_D else 0.0) for m in models)
     q_ms = prof["ms"]["proj_q"] / max(1, prof["steps"])
     peak, note = tensor_peak("tf32", bf16_burst, peak_src, measured)
     share = {k: round(v / max(1e-9, sum(prof["ms"].values())), 4) for k, v in prof["ms"].items()}
     return {"workload": "sweep256: 256 Ising instances, beta ~ U[0.35, 0.55], D_cut in {16, 24, 32, 40}, TF32",
             "value": round(n * steps / (ms / 1e3), 3), "unit": "RG-steps/s (instance-steps/s)",
             "ms_per_batch_step": round(ms / steps, 3), "steps_timed": steps,
-            "roofline": {"kernel": "k_tc_gemm a6 (all cut groups of a step)", "bound": "tensor",
+            "roofline": {"kernel": "bond contraction stage of all cut groups of a step (k_tc_chain "
+                                   "a6 + a7 for D_cut 16 and 32, k_tc_gemm a6 for 24 and 40)", "bound": "tensor",
                          "achieved": round(q_flops / (q_ms / 1e3) / 1e12, 2), "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(q_flops / (q_ms / 1e3) / 1e12 / peak, 4),
                          "peak_source": note},
@@ -714,7 +770,9 @@ def run_sweep(args, world, rank, local):
     value = n * args.steps / (max_ms / 1e3)
     lz_all = gather_floats(lz_mine, world)
     flops_step = sum(step_flops(m.D_cut, m.D_cut, m.D_cut) for m in models)
-    q_flops = sum(2.0 * m.D_cut ** 7 for m in models)          # a6 flops of one batch step
+    # bond-contraction stage flops of one batch step (a7 too where the fused kernel runs)
+    q_flops = sum(2.0 * m.D_cut ** 7 + (2.0 * m.D_cut ** 6 if prec == "tf32" and m.D_cut in FUSED_D else 0.0)
+                  for m in models)
     q_ms_step = prof["ms"]["proj_q"] / max(1, prof["steps"])
     achieved = q_flops / (q_ms_step / 1e3) / 1e12
     bf16_burst, _, _, peak_src = peaks()
@@ -734,7 +792,8 @@ def run_sweep(args, world, rank, local):
                       "parallelism": f"instance-sharded x{world}"},
            "tflops": round(sum(step_flops(m.D_cut, m.D_cut, m.D_cut) for m in everything)
                            * args.steps / (max_ms / 1e3) / 1e12, 3),
-           "roofline": {"kernel": "k_tc_gemm a6 bond contraction Q=P.T (all groups of a step)",
+           "roofline": {"kernel": "bond contraction stage of all groups of a step (k_tc_chain a6 + a7 "
+                                  "where fused, else k_tc_gemm a6)",
                         "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                         "peak_source": f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"},

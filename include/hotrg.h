@@ -320,16 +320,26 @@ hotrg_status hotrg_dims(hotrg_ctx *ctx, int *Dx, int *Dy, int *nsteps);
  *       HOTRG_ETIMEOUT.  Process-wide (every context), for launches made after
  *       the call; segments already captured into CUDA graphs keep the bound
  *       they were captured with.
- *   HOTRG_OPT_TEST_STALL  1: testing aid for the timeout path.  The next
- *       tensor-core GEMM launched in the process (by any context) issues no
+ *   HOTRG_OPT_TEST_STALL  1 or 2: testing aid for the timeout path.  The next
+ *       tensor-core kernel launched in the process (by any context) of the
+ *       chosen kind -- 1: a GEMM, 2: the fused a6 -> a7 kernel -- issues no
  *       operand copies, so its pipeline waits find a barrier nothing arrives at
  *       and run out after HOTRG_OPT_WAIT_CYCLES; one-shot.
+ *   HOTRG_OPT_FUSED_CHAIN  0 (default) / 1: with 1, HOTRG_TF32 steps with
+ *       Dx = Dy in {16, 32} and D' <= 32 run the products Q = P T and
+ *       T' = Q U (Sec. II.B, Eq. 3) as one kernel that keeps Q in on-chip
+ *       memory (the second product sums over (x1', x2') in another order, so
+ *       results differ from the unfused chain by FP32 rounding).  It saves
+ *       Q's write and read (2 x 4 D^5 bytes) but is slower on GB300 (its
+ *       second product has N = 16, and such MMAs take the tensor pipe about as
+ *       long as N = 128 ones), hence off by default; 0 runs the two GEMMs with
+ *       Q in device memory.
  * Returns HOTRG_EINVAL for an unknown option or value.
  */
 enum {
   HOTRG_OPT_EIG_TC_PRODUCTS = 0, HOTRG_OPT_XS_DIGITS = 1, HOTRG_OPT_GEMM_AUTOTUNE = 2,
   HOTRG_OPT_GRAPHS = 3, HOTRG_OPT_EIG_MAX_ITERS = 4, HOTRG_OPT_WAIT_CYCLES = 5,
-  HOTRG_OPT_TEST_STALL = 6
+  HOTRG_OPT_TEST_STALL = 6, HOTRG_OPT_FUSED_CHAIN = 7
 };
 hotrg_status hotrg_set_option(hotrg_ctx *ctx, int option, int value);
 

@@ -31,6 +31,7 @@ OPT_GRAPHS = 3
 OPT_EIG_MAX_ITERS = 4
 OPT_WAIT_CYCLES = 5
 OPT_TEST_STALL = 6
+OPT_FUSED_CHAIN = 7
 WAIT_CYCLES_DEFAULT = 2_000_000_000
 
 

@@ -234,8 +234,8 @@ struct Group {
   // direction, D, E, D', address of T, profiler on): the key fixes every
   // launch's arguments, and T alternates between two buffers, so a
   // steady-state run replays two graphs per segment.
-  std::map<std::array<long long, 7>, SegGraph> graphs;
-  std::set<std::array<long long, 7>> seen, nograph;
+  std::map<std::array<long long, 8>, SegGraph> graphs;
+  std::set<std::array<long long, 8>> seen, nograph;
   // Work of the group's steps: its own stream (the context's stream when the
   // context holds one group), stage profiler and eigensolver workspace, so
   // that the groups of a batch can step concurrently.
@@ -272,6 +272,7 @@ struct hotrg_ctx {
   std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
   bool eig_tc = true;                       // exact-slice tensor-core products G X
   bool use_graphs = true;                   // replay contraction segments as CUDA graphs
+  bool fuse_chain = false;                  // fused a6 -> a7 kernel where its shapes allow
   int xs_digits = 6;                        // digits of the exact-slice contraction mode
   int eig_max_iters = 80;                   // subspace iterations before HOTRG_EEIG
   int *err = nullptr;
@@ -540,8 +541,9 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   // separate graph from the unprofiled one) and timed after each replay.
   auto run_segment = [&](int seg, const std::function<int(StageHook *)> &body) -> int {
     if (!c->use_graphs || st == nullptr) return body(&pf);
-    const std::array<long long, 7> key{seg, (long long)dir, D, E, Dn,
-                                       (long long)reinterpret_cast<uintptr_t>(g.T), pf.on ? 1 : 0};
+    const std::array<long long, 8> key{seg, (long long)dir, D, E, Dn,
+                                       (long long)reinterpret_cast<uintptr_t>(g.T), pf.on ? 1 : 0,
+                                       c->fuse_chain ? 1 : 0};
     auto it = g.graphs.find(key);
     if (it != g.graphs.end()) {
       for (int k = 0; k < HOTRG_NSTAGES; ++k)
@@ -748,7 +750,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   if (tc) {
     if (int r = run_segment(1, [&](StageHook *hook) {
           return g.tc.project(g.T, g.sT, g.U, g.sU, D, E, Dn, sx, sxp, sy, syp, g.Tn, g.sT, tm, tn,
-                              hook);
+                              c->fuse_chain, hook);
         }))
       return fail(c, HOTRG_ECUDA, std::string("tensor-core projection chain failed: ") +
                                       cudaGetErrorString(static_cast<cudaError_t>(r)));
@@ -1044,8 +1046,12 @@ hotrg_status hotrg_set_option(hotrg_ctx *c, int option, int value) {
       tc::set_wait_limit(value);
       return HOTRG_OK;
     case HOTRG_OPT_TEST_STALL:
-      if (value != 1) return HOTRG_EINVAL;
-      tc::arm_stall();
+      if (value != 1 && value != 2) return HOTRG_EINVAL;
+      tc::arm_stall(value == 1 ? tc::kStallGemm : tc::kStallChain);
+      return HOTRG_OK;
+    case HOTRG_OPT_FUSED_CHAIN:
+      if (value != 0 && value != 1) return HOTRG_EINVAL;
+      c->fuse_chain = value != 0;
       return HOTRG_OK;
   }
   return HOTRG_EINVAL;

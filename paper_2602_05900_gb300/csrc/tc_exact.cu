@@ -458,7 +458,7 @@ cudaError_t launch_xs(const XsOperand &A, const XsOperand &B, int M, int N, int 
   const int batch = A.batch < 1 ? 1 : A.batch;
   dim3 grid(ntn * ksplit, (M + C::BM - 1) / C::BM, batch);
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
-  const int stall = take_stall() ? 1 : 0;
+  const int stall = take_stall(kStallGemm) ? 1 : 0;
   k_xs_gemm<S, BN><<<grid, 128, C::SMEM, s>>>(ta, tb, M, N, K, kbp, ntn, o, err, wait_limit(),
                                               stall);
   return cudaGetLastError();

@@ -360,7 +360,7 @@ bool make_map(CUtensorMap *m, TcMode mode, const TcOperand &op, int box_rows) {
 template <int MODE, int BN>
 cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int batch,
                    const TcEpilogue &epi, int *err, cudaStream_t s) {
-  const int stall = take_stall() ? 1 : 0;
+  const int stall = take_stall(kStallGemm) ? 1 : 0;
   using C = Cfg<MODE, BN>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -471,13 +471,16 @@ namespace tc {
 
 namespace {
 std::atomic<long long> g_wait_limit{kWaitCycles};
-std::atomic<bool> g_stall{false};
+std::atomic<int> g_stall{0};
 }  // namespace
 
 void set_wait_limit(long long cycles) { g_wait_limit.store(cycles > 0 ? cycles : kWaitCycles); }
 long long wait_limit() { return g_wait_limit.load(); }
-void arm_stall() { g_stall.store(true); }
-bool take_stall() { return g_stall.exchange(false); }
+void arm_stall(int kind) { g_stall.store(kind); }
+bool take_stall(int kind) {
+  int k = kind;
+  return g_stall.compare_exchange_strong(k, 0);
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

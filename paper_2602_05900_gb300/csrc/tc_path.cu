@@ -9,6 +9,7 @@
 // separate pass.
 #include <cuda_bf16.h>
 
+#include "tc_chain.cuh"
 #include "tc_gemm.cuh"
 #include "tc_path.cuh"
 
@@ -217,36 +218,70 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
 
 int TcPath::project(const double *T, long long sT, const double *U, long long sU, int D, int E,
                     int Dn, long long sx, long long sxp, long long sy, long long syp, double *Tout,
-                    long long sTout, IdxMap tm, IdxMap tn, StageHook *hook) {
+                    long long sTout, IdxMap tm, IdxMap tn, bool fuse, StageHook *hook) {
   Impl &I = *impl_;
+  fuse = fuse && I.mode == TcMode::TF32 && tc_chain_supported(D, E, Dn);
   const int n = D * D, DE = D * E, E2 = E * E;
   const int p5 = tc_pitch(D, I.mode), p6 = tc_pitch(DE, I.mode), p7 = tc_pitch(n, I.mode);
   if ((std::size_t)D * Dn * p5 > I.capT || (std::size_t)D * E2 * p5 > I.capT ||
       (std::size_t)DE * p6 > I.capT || (std::size_t)Dn * p7 > I.capT ||
       (std::size_t)Dn * DE * p6 > I.capP || (std::size_t)Dn * E2 * p7 > I.capP)
     return cudaErrorInvalidValue;
-  // a1: operands of a5 (U and T views with the x1 axis as K), a6 (T view) and a7 (U^T)
+  // a1: operands of a5 (U and T views with the x1 axis as K), a6 (T view) and a7 (U^T;
+  // the fused kernel reads its K axis (x1', x2') in the order x2', x1')
   hook->begin(HOTRG_ST_PREP);
   if (cudaError_t e_ = gather(I, U, sU, D * Dn, D, p5, map2(Dn, n, 1), map1(D), I.opU5)) return e_;
   if (cudaError_t e_ = gather(I, T, sT, D * E2, D, p5, map3(E, E, syp, sy, sxp), map1(sx), I.opT5))
     return e_;
   if (cudaError_t e_ = gather(I, T, sT, DE, DE, p6, map2(D, sxp, syp), map2(E, sy, sx), I.opT6))
     return e_;
-  if (cudaError_t e_ = gather(I, U, sU, Dn, n, p7, map1(n), map1(1), I.opU7)) return e_;
+  if (cudaError_t e_ = gather(I, U, sU, Dn, n, p7, map1(n), fuse ? map2(D, D, 1) : map1(1), I.opU7))
+    return e_;
   hook->launched(HOTRG_ST_PREP, 4);
   hook->end(HOTRG_ST_PREP);
 
-  // a5: P[(a,x1',y)][(x2,k)] = sum_x1 U[(x1 x2),a] T[x1,x1',y,k]; rows m = (x2,a), cols (x1',y,k)
+  // a5: P[(a,x1',y)][(x2,k)] = sum_x1 U[(x1 x2),a] T[x1,x1',y,k]; rows m = (x2,a), cols (x1',y,k).
+  // The fused kernel wants P's rows in the order (a, y, x1').
   hook->begin(HOTRG_ST_PROJ_P);
   {
     TcOperand a = operand(I, I.opU5, D * Dn, D, p5, I.sTop), b = operand(I, I.opT5, D * E2, D, p5, I.sTop);
     const long long ps = (long long)Dn * DE * p6;
-    TcEpilogue ep = operand_epilogue(I, I.P, ps, map2(Dn, (long long)DE * p6, E),
-                                     map3(E, E, 1, p6, (long long)E * p6), I.sPop);
+    const IdxMap pn = fuse ? map3(E, E, 1, (long long)D * p6, p6) : map3(E, E, 1, p6, (long long)E * p6);
+    TcEpilogue ep = operand_epilogue(I, I.P, ps, map2(Dn, (long long)DE * p6, E), pn, I.sPop);
     if (cudaError_t e_ = tc_gemm(I.mode, a, b, D * Dn, D * E2, D, ep, I.err, I.s)) return e_;
   }
   hook->launched(HOTRG_ST_PROJ_P, 1);
   hook->end(HOTRG_ST_PROJ_P);
+  if (fuse) {
+    // a6 + a7 in one kernel (its time is reported under the a6 stage)
+    hook->begin(HOTRG_ST_PROJ_Q);
+    ChainArgs ca{};
+    ca.D = D;
+    ca.E = E;
+    ca.Dn = Dn;
+    ca.batch = I.G;
+    ca.P = static_cast<const float *>(I.P);
+    ca.pitchP = p6;
+    ca.sP = I.sPop;
+    ca.T6 = static_cast<const float *>(I.opT6);
+    ca.pitchT = p6;
+    ca.sT6 = I.sTop;
+    ca.U7 = static_cast<const float *>(I.opU7);
+    ca.pitchU = p7;
+    ca.sU7 = I.sTop;
+    ca.Tout = Tout;
+    ca.sTout = sTout;
+    ca.tm = tm;
+    ca.tn = tn;
+    ca.cap = sTout * I.G;
+    ca.err = I.err;
+    if (cudaError_t e_ = tc_chain(ca, I.s)) return e_;
+    hook->launched(HOTRG_ST_PROJ_Q, 1);
+    hook->end(HOTRG_ST_PROJ_Q);
+    hook->begin(HOTRG_ST_PROJ_T);
+    hook->end(HOTRG_ST_PROJ_T);
+    return 0;
+  }
   // a6: Q[(a,y,y')][(x1',x2')] = sum_{x2,k} P[(a,x1',y),(x2,k)] T[x2,x2',k,y']
   hook->begin(HOTRG_ST_PROJ_Q);
   {

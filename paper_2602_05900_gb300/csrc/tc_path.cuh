@@ -25,10 +25,11 @@ class TcPath {
                   long long sy, long long syp, double *GL, double *GR, long long sG,
                   StageHook *hook);
   // a5 - a7: T'(m, b) = [U^T (T.T) U], written in FP64 through the maps (tm, tn)
-  // at Tout + i * sTout.
+  // at Tout + i * sTout.  fuse: a6 and a7 as one kernel (Q kept on chip) where
+  // tc_chain_supported(D, E, Dn) and the mode is TF32.
   int project(const double *T, long long sT, const double *U, long long sU, int D, int E, int Dn,
               long long sx, long long sxp, long long sy, long long syp, double *Tout,
-              long long sTout, IdxMap tm, IdxMap tn, StageHook *hook);
+              long long sTout, IdxMap tm, IdxMap tn, bool fuse, StageHook *hook);
 
   struct Impl;
 

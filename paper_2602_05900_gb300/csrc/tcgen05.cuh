@@ -138,11 +138,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 // launched from now on (kernels already captured into CUDA graphs keep theirs).
 void set_wait_limit(long long cycles);
 long long wait_limit();
-// Test hook: the next tensor-core GEMM launched in the process issues no
-// operand copies, so its pipeline waits run out (a barrier nothing arrives
-// at) and it reports a timeout through its error flag.  One-shot.
-void arm_stall();
-bool take_stall();
+// Test hook: the next tensor-core kernel of the given kind launched in the
+// process (kStallGemm: a GEMM, plain or exact-slice; kStallChain: the fused
+// projection) issues no operand copies, so its pipeline waits run out (a
+// barrier nothing arrives at) and it reports a timeout through its error
+// flag.  One-shot.
+constexpr int kStallGemm = 1, kStallChain = 2;
+void arm_stall(int kind);
+bool take_stall(int kind);
 
 }  // namespace tc
 }  // namespace hotrg

@@ -2,7 +2,8 @@
 which this GPU pool does not offer).
 
 The library is rebuilt with -DHOTRG_CHECKED=1: every mapped access of the
-FP64 GEMMs, the operand gathers and the tensor-core epilogues is compared with
+FP64 GEMMs, the operand gathers, the tensor-core epilogues and the fused
+projection kernel's output stores is compared with
 the capacity of its buffer, and an access outside it is skipped and reported as
 HOTRG_EBOUNDS instead of being performed.  The checked library runs, in a child
 process (a process loads one build), the step paths of every precision mode on
@@ -41,6 +42,14 @@ with pkg.HotrgBatch(T0s, [8, 12, 8], "fp64") as bt:
 for T0, D, v in zip([0.42, 0.46, 0.44], [8, 12, 8], lz):
     want = ref.run(ref.ising_initial_tensor(T0), D, 8).ln_z_per_site
     assert abs(v / want - 1) < 1e-12, (T0, D, v, want)
+# TF32 batch with the fused projection kernel on (the D_cut = 16 group runs it)
+from paper_2602_05900_gb300.capi import OPT_FUSED_CHAIN
+with pkg.HotrgBatch(T0s, [16, 12, 16], "tf32") as bt:
+    bt.set_option(OPT_FUSED_CHAIN, 1)
+    lz = bt.run(8).ln_z_per_site()
+for T0, D, v in zip([0.42, 0.46, 0.44], [16, 12, 16], lz):
+    want = ref.run(ref.ising_initial_tensor(T0), D, 8).ln_z_per_site
+    assert abs(v / want - 1) < 5e-4, (T0, D, v, want)     # TF32 whole-job bound (beta = 0.44 is near critical)
 print("CHECKED_OK")
 """
 

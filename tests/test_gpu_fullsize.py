@@ -98,11 +98,16 @@ def run_to_steady(pkg, cfg, prec):
 
 
 @pytest.mark.parametrize("name,prec", [("ising_044h_d48", "fp64"), ("ising_044_d32", "fp64"),
-                                       ("ising_044h_d48", "tf32"), ("ising_044_d32", "tf32")])
+                                       ("ising_044h_d48", "tf32"), ("ising_044_d32", "tf32"),
+                                       ("ising_044_d32", "tf32-fused")])
 def test_sampled_full_size_step(pkg, name, prec):
+    from paper_2602_05900_gb300.capi import OPT_FUSED_CHAIN
     cfg = CONFIGS[name]
+    fused = prec == "tf32-fused"            # the fused a6 -> a7 kernel (Q kept on chip)
+    prec = "tf32" if fused else prec
     h, d = run_to_steady(pkg, cfg, prec)
     with h:
+        h.set_option(OPT_FUSED_CHAIN, 1 if fused else 0)
         T_in = h.tensor()                                   # normalised input of the step
         h.step(d)
         i = h.dims()[2] - 1
