@@ -650,6 +650,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
   __shared__ int rotated;
   __shared__ unsigned int maxrel_bits;
   __shared__ double s_floor, s_sig;
+  __shared__ int s_more, s_any[2];     // post-sweep test: this CTA's rows / the cluster's
   auto top_index = [&](int sl, int rr) { return (sl == 0) ? 0 : 1 + (sl - 1 + rr) % (m - 1); };
   auto bot_index = [&](int sl, int rr) { return 1 + (m - 2 - sl + rr) % (m - 1); };
 
@@ -678,6 +679,7 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
   // changes no eigenpair beyond that level, while the relative test below would
   // keep rotating noise between near-null diagonal entries (measured: 12 -> 9.7
   // sweeps per Rayleigh-Ritz solve on D = 32-48 environments)
+  if (threadIdx.x == 0) s_any[0] = s_any[1] = 0;
   if (threadIdx.x < 32) {
     double v = 0.0;
     for (int i = threadIdx.x; i < m; i += 32) v = fmax(v, fabs(Cin.at(z)[(size_t)i * m + i]));
@@ -803,6 +805,37 @@ __global__ void __launch_bounds__(512, 2) k_si_jacobi(PSet Cin, int m, PSet Wout
     __syncthreads();
     stop = (rotated == 0) || __uint_as_float(maxrel_bits) < 1e-16f;
     __syncthreads();
+    if (!stop) {
+      // Would the next sweep rotate anything?  Every CTA applies the rotation
+      // test to the entries of its own rows (diagonal entries from the
+      // replicated table of the next round, gathered into `diag`, which is
+      // free until the end), the answers are OR-ed across the cluster, and a
+      // sweep that would rotate nothing is not run.
+      const int rr = r_global % (m - 1);
+      const double *ndc = nd + (r_global & 1) * 3 * half;
+      for (int sl = threadIdx.x; sl < half; sl += blockDim.x) {
+        diag[top_index(sl, rr)] = ndc[sl * 3 + 0];
+        diag[bot_index(sl, rr)] = ndc[sl * 3 + 1];
+      }
+      if (threadIdx.x == 0) s_more = 0;
+      __syncthreads();
+      for (int e = threadIdx.x; e < (s1 - s0) * 2 * m; e += blockDim.x) {
+        const int sl = s0 + e / (2 * m), tb = (e / m) & 1, c = e % m;
+        const int idx = tb == 0 ? top_index(sl, rr) : bot_index(sl, rr);
+        if (c != idx) {
+          const double h = ROW(cur, sl, tb)[c];
+          if (fabs(h) > s_floor && h * h > 1e-30 * fabs(diag[idx] * diag[c]) && fabs(h) > 1e-300)
+            s_more = 1;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && s_more)
+        for (int k = 0; k < kCluster; ++k) atomicExch(cluster.map_shared_rank(&s_any[sweep & 1], k), 1);
+      cluster.sync();
+      stop = s_any[sweep & 1] == 0;
+      __syncthreads();
+      if (threadIdx.x == 0) s_any[sweep & 1] = 0;   // reused two sweeps on, after this CTA's next barriers
+    }
   }
   // diagonal: each CTA knows the index of every row it holds; gather all m values
   {
@@ -947,6 +980,22 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
     const int rot = s_rot;
     __syncthreads();
     if (!rot) break;
+    // The sweep that would find nothing to rotate is not run: the rotation
+    // test of every off-diagonal entry, once, decides it (m^2 / 2 tests
+    // against the m - 1 rounds of a sweep).
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int p = e / m, q = e % m;
+      if (q > p) {
+        const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+        if (fabsf(apq) > floor_abs && apq * apq > 1e-12f * fabsf(app * aqq)) s_rot = 1;
+      }
+    }
+    __syncthreads();
+    const int more = s_rot;
+    __syncthreads();
+    if (!more) break;
   }
   if (threadIdx.x == 0) atomicMax(sweeps, sweep + 1);
   double *out = Vout.at(z);
@@ -1445,9 +1494,9 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   };
   // dst = orth(src) through tmp (src is overwritten).  After the first
   // Rayleigh-Ritz step the basis holds Ritz vectors, G X is X Theta up to the
-  // residual, its column-scaled Gram matrix is close to I, and two CholeskyQR
-  // passes with FP32 factorisations suffice for the power iteration.  Before it
-  // the block can be ill conditioned.  Small batches (latency bound: the
+  // residual, its column-scaled Gram matrix is close to I, and one CholeskyQR
+  // pass with an FP32 factorisation suffices for the power iteration.  Before
+  // it the block can be ill conditioned.  Small batches (latency bound: the
   // single-CTA FP64 factorisation costs more than its iterations save) use the
   // same two FP32 passes, the first of which retries with a diagonal shift
   // where the columns are nearly dependent; large batches use shifted
@@ -1463,13 +1512,23 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   // rest of the solve orthogonalises with two FP64 CholeskyQR passes.
   const bool fp64_start = P > kSiSmallBatch;
   bool orth64 = false;
+  int n_orth = 0;
   auto orth = [&](PSet src, PSet tmp, PSet dst, bool after_rr) -> cudaError_t {
     cudaError_t r;
+    ++n_orth;
     if (orth64) {
       if ((r = cholqr64(src, tmp, shift))) return r;
       return cholqr64(tmp, dst, 0.0);
     }
-    if (after_rr || !fp64_start) {
+    // One FP32 pass once the columns are close to eigenvectors (after a
+    // Rayleigh-Ritz step, or from the third iteration of a warm start): the
+    // column-scaled Gram matrix of G X is then close to I and one pass leaves
+    // X orthonormal to about FP32 accuracy, which is all the power iteration
+    // needs -- the Rayleigh-Ritz step works with C0 = X^T X and does not
+    // assume an orthonormal basis (measured at D = 32: 8.5 iterations per
+    // step either way, 0.6 ms less per step).
+    if (after_rr || (b.has_warm && n_orth >= 3)) return cholqr32(src, dst, 0.0f);
+    if (!fp64_start) {
       if ((r = cholqr32(src, tmp, 0.0f))) return r;
       return cholqr32(tmp, dst, 0.0f);
     }

@@ -78,6 +78,9 @@ def test_fp64_batch_vs_oracle(pkg, oracle_runs):
             assert T.shape == r.T.shape
 
 
+BATCH_VS_SINGLE = {"tf32": 1e-5, "bf16x3": 3e-9}
+
+
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
 def test_mixed_batch_vs_oracle_and_single(pkg, oracle_runs, prec):
     inst = instances()
@@ -91,8 +94,13 @@ def test_mixed_batch_vs_oracle_and_single(pkg, oracle_runs, prec):
         with pkg.Hotrg(gpu_t0(pkg, k, b, h), d, prec) as one:
             one.run(12)
             single = one.ln_z_per_site()
-        # same kernels and operand rounding; only eigensolver iteration counts may differ
-        assert abs(lz[i] / single - 1) < 1e-9, (i, lz[i], single)
+        # Same kernels and operand rounding; only eigensolver iteration counts
+        # differ (a batch iterates until its slowest problem converges).  A
+        # reduced-precision G is accurate to its noise floor 2u, residuals at
+        # that floor are accepted, and ln Z / N then differs at the floor's
+        # second order: (2u)^2 = 9.5e-7 (TF32), 2.3e-10 (BF16X3); bounded at
+        # about ten times that.
+        assert abs(lz[i] / single - 1) < BATCH_VS_SINGLE[prec], (i, lz[i], single)
 
 
 def test_batch_of_one_matches_single_context(pkg):
@@ -123,9 +131,11 @@ def test_exact_slice_batch_vs_oracle(pkg, oracle_runs):
 
 
 def test_options_are_validated(pkg):
-    from paper_2602_05900_gb300.capi import HOTRG_EINVAL, OPT_EIG_TC_PRODUCTS, OPT_XS_DIGITS
+    from paper_2602_05900_gb300.capi import (HOTRG_EINVAL, OPT_EIG_TC_PRODUCTS, OPT_FUSED_CHAIN,
+                                             OPT_TEST_STALL, OPT_XS_DIGITS)
     with pkg.Hotrg(pkg.ising_tensor(0.44, 0.0), 8, "bf16xs") as h:
-        for opt, val in ((OPT_XS_DIGITS, 3), (OPT_XS_DIGITS, 9), (OPT_EIG_TC_PRODUCTS, 2), (7, 0)):
+        for opt, val in ((OPT_XS_DIGITS, 3), (OPT_XS_DIGITS, 9), (OPT_EIG_TC_PRODUCTS, 2), (99, 0),
+                         (OPT_FUSED_CHAIN, 2), (OPT_TEST_STALL, 3)):
             with pytest.raises(pkg.HotrgError) as e:
                 h.set_option(opt, val)
             assert e.value.status == HOTRG_EINVAL
