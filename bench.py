@@ -365,6 +365,9 @@ def run_ours(args, world, rank, local):
     measured = measure_peaks(torch) if rank == 0 else {}
 
     h, d = steady_job(pkg, cfg, prec, stream, autotune=not args.no_autotune)
+    if args.fused_chain:
+        from paper_2602_05900_gb300.capi import OPT_FUSED_CHAIN
+        h.set_option(OPT_FUSED_CHAIN, 1)
     _, d = time_steps(torch, h, d, args.warmup, stream, flush)
     n_before = h.dims()[2]
     h.profile_enable(True)
@@ -386,9 +389,9 @@ def run_ours(args, world, rank, local):
     value = world * args.steps / (max_ms / 1e3)
     bf16_burst, bf16_sust, hbm, peak_src = peaks()
 
-    # dominant contraction kernel, one launch per step: the a6 GEMM Q = P.T (the
-    # fused a6 + a7 kernel is an option, off by default: see the fused_chain block)
-    fused = False
+    # dominant contraction kernel, one launch per step: the a6 GEMM Q = P.T, or with
+    # --fused-chain the fused a6 + a7 kernel (off by default: see the fused_chain block)
+    fused = bool(args.fused_chain) and prec == "tf32" and D in FUSED_D
     q_ms = prof["ms"]["proj_q"] / max(1, prof["stage_launches"]["proj_q"])
     q_flops = 2.0 * D ** 7 + (2.0 * D ** 6 if fused else 0.0)
     achieved = q_flops / (q_ms / 1e3) / 1e12
@@ -1217,6 +1220,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed GEMM tile widths (profiling: the autotuner's timings are distorted under ncu)")
+    ap.add_argument("--fused-chain", action="store_true",
+                    help="run the headline steps with the fused a6 + a7 kernel (HOTRG_OPT_FUSED_CHAIN = 1)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
