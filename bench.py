@@ -344,7 +344,7 @@ def eig_block(prof, steps, D, measured, info):
             "subspace_iterations_per_step": mean([i.eig_iters for i in sub]),
             "rayleigh_ritz_per_step": mean([i.eig_rr for i in sub]),
             "jacobi_sweeps_fp32_per_rr": mean([i.eig_sweeps32 for i in sub]),
-            "jacobi_sweeps_fp64_per_rr": mean([i.eig_sweeps for i in sub]),
+            "fp64_finish_jacobi_rounds_per_rr": mean([i.eig_sweeps for i in sub]),
             "dense_fp64_tridiagonalisation_flops": dense,
             "dense_fp64_lower_bound_ms": round(dense / (fp64 * 1e12) * 1e3, 4),
             "fp64_peak_tflops": fp64,

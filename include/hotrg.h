@@ -106,7 +106,9 @@ typedef struct {
   int eig_iters;    /* subspace iterations (path 2)                                */
   double eig_residual; /* max_i<=D' ||G u_i - lambda_i u_i|| / lambda_1 (path 2)    */
   int eig_rr;       /* Rayleigh-Ritz steps of the subspace iteration (path 2)      */
-  int eig_sweeps;   /* most FP64 Jacobi sweeps of one Rayleigh-Ritz step (path 2)  */
+  int eig_sweeps;   /* most rounds of the FP64 finishing Jacobi of one Rayleigh-Ritz
+                       step (path 2): rotations still needed after the first-order
+                       corrections (0: none)                                        */
   int eig_sweeps32; /* most FP32 Jacobi sweeps of one Rayleigh-Ritz step (path 2)  */
 } hotrg_step_info_t;
 

@@ -343,16 +343,19 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     // Blocked right-looking factorisation, panels of kCholPanel columns and two
-    // barriers per panel: (a) every thread factors the panel's diagonal block
-    // U^T U = C_jj redundantly in registers (identical inputs, identical
-    // results, so a failed pivot stops every thread alike); (b) the panel's rows
-    // of R right of the block, U^T R_j,rest = C_j,rest, by forward substitution,
-    // one column per thread; (c) the trailing update C_rest -= R_j,rest^T R_j,rest.
+    // barriers per panel: (a) the threads of the first three warps (the ones
+    // that need it: m <= 96) factor the panel's diagonal block U^T U = C_jj
+    // redundantly in registers (identical inputs, identical results); (b) the
+    // panel's rows of R right of the block, U^T R_j,rest = C_j,rest, by forward
+    // substitution, one column per thread; (c) after the barrier, a failed pivot
+    // (published by thread 0) stops every thread, else the trailing update
+    // C_rest -= R_j,rest^T R_j,rest.
+    const bool factor = threadIdx.x < 96;
     for (int j0 = 0; j0 < m; j0 += kCholPanel) {
       const int w = min(kCholPanel, m - j0);
       float U[kCholPanel][kCholPanel];
       float uinv[kCholPanel];
-      bool ok = true;
+      bool ok = factor;
 #pragma unroll
       for (int i = 0; i < kCholPanel; ++i) {
         if (i < w && ok) {
@@ -377,11 +380,8 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
           }
         }
       }
-      if (!ok) {
-        if (threadIdx.x == 0) bad = 1;
-        break;
-      }
-      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      if (factor && !ok && threadIdx.x == 0) bad = 1;
+      for (int e = threadIdx.x; ok && e < w * w; e += blockDim.x) {
         const int i = e / w, b = e % w;
         if (b >= i) {
           float v = 0.0f;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
           R[(j0 + i) * ld + j0 + b] = v;
         }
       }
-      for (int l = j0 + w + threadIdx.x; l < m; l += blockDim.x) {
+      for (int l = j0 + w + threadIdx.x; ok && l < m; l += blockDim.x) {
         float y[kCholPanel];
 #pragma unroll
         for (int i = 0; i < kCholPanel; ++i) {
@@ -407,12 +407,20 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
         }
       }
       __syncthreads();
-      for (int a = j0 + w + ty; a < m; a += 16)
+      if (bad) break;
+      // a panel with a trailing part is a full one (w = kCholPanel); the
+      // thread's column a of the panel rows stays in registers
+      for (int a = j0 + w + ty; a < m; a += 16) {
+        float ra[kCholPanel];
+#pragma unroll
+        for (int i = 0; i < kCholPanel; ++i) ra[i] = R[(j0 + i) * ld + a];
         for (int b = a + tx; b < m; b += 16) {
           float v = C[a * ld + b];
-          for (int i = 0; i < w; ++i) v = fmaf(-R[(j0 + i) * ld + a], R[(j0 + i) * ld + b], v);
+#pragma unroll
+          for (int i = 0; i < kCholPanel; ++i) v = fmaf(-ra[i], R[(j0 + i) * ld + b], v);
           C[a * ld + b] = v;
         }
+      }
       __syncthreads();
     }
     __syncthreads();
@@ -1005,6 +1013,176 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
   }
 }
 
+// ---- FP64 finish of the Rayleigh-Ritz eigensolver --------------------------
+//
+// After the FP32 stage, H' = V^T H V is diagonal to FP32 accuracy: its
+// off-diagonal entries e_ij are ~1e-7 of their diagonal pair.  Two steps of a
+// simultaneous first-order correction remove them for every pair whose
+// diagonal entries are well separated: with A_ij = e_ij / (d_j - d_i) (skew
+// symmetric), Q = orth(I + A + A^2 / 2) (one Newton-Schulz step) and
+// H' <- Q^T H' Q, the remaining coupling of such a pair is of order
+// e_ij^2 / (d_j - d_i); the second step takes it to rounding level.  These are
+// dense m x m FP64 products spread over many CTAs (k_rr_mm).  Pairs inside a
+// cluster of near-equal diagonal entries (|d_j - d_i| <= kSfsCluster |e_ij|)
+// are left out of A and resolved afterwards by exact 2 x 2 rotations
+// (Eq. 6) of the sparse Jacobi below, which only rotates the pairs that still
+// need it.  This replaces the full sweeps of the cluster Jacobi (2 sweeps x
+// (m - 1) rounds) on the nearly diagonal H'.
+constexpr double kSfsCluster = 1e3;
+
+__global__ void k_rr_sfs_build(PSet Hp, int m, PSet Aout) {
+  const int z = blockIdx.z;
+  const double *h = Hp.at(z);
+  double *a = Aout.at(z);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e % m, j = e / m;                      // column-major: a[i + j m]
+    double v = 0.0;
+    if (i != j) {
+      const double eij = 0.5 * (h[(size_t)j * m + i] + h[(size_t)i * m + j]);
+      const double gap = h[(size_t)j * m + j] - h[(size_t)i * m + i];
+      if (eij != 0.0 && fabs(gap) > kSfsCluster * fabs(eij)) v = eij / gap;
+    }
+    a[e] = v;
+  }
+}
+
+// Classical-order ("largest first") two-sided Jacobi on the nearly diagonal
+// symmetric m x m matrix Hin (one CTA per problem): each round, every row
+// finds the partner with the largest entry that needs rotating (the rotation
+// test of k_si_jacobi: above 2^-44 of the largest diagonal entry and not
+// negligible against its own diagonal pair), the mutually largest pairs --
+// disjoint by construction, and always including the largest entry of the
+// matrix -- are rotated at once (Eq. 6), and the accumulated rotation W (in:
+// Win, m x m column-major) follows.  Stops when nothing needs rotating;
+// *rounds receives the round count (maximum over problems), flag is set to 2
+// if kSparseRounds * m rounds do not suffice.  Output as k_si_jacobi: Ritz
+// values descending in theta, Wout columns in the same order.
+constexpr int kSparseRounds = 16;
+constexpr int kSparseThreads = 1024;
+
+size_t sparse_smem(int m) {
+  return (size_t)2 * m * (m + 1) * sizeof(double) + (size_t)m * (sizeof(int) + sizeof(double)) +
+         (size_t)(m / 2 + 1) * (2 * sizeof(int) + 2 * sizeof(double)) + 64;
+}
+
+__global__ void __launch_bounds__(kSparseThreads, 1)
+    k_rr_sparse_jacobi(PSet Hin, int m, PSet Win, PSet Wout, PSet theta, int *flag, int *rounds_out) {
+  extern __shared__ double ssh[];
+  const int ld = m + 1, maxsel = m / 2 + 1;
+  double *H = ssh;                                  // row-major, symmetric part of Hin
+  double *W = H + (size_t)m * ld;                   // W[r * ld + c] = Win(r, c)
+  double *sc = W + (size_t)m * ld;                  // rotation c of selected pair k
+  double *ss = sc + maxsel;                         // rotation s
+  int *best = reinterpret_cast<int *>(ss + maxsel); // per row: partner with the largest entry, -1
+  int *selp = best + m, *selq = selp + maxsel;
+  __shared__ int nsel;
+  __shared__ double s_floor;
+  const int z = blockIdx.z;
+  const double *hin = Hin.at(z), *win = Win.at(z);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int r = e / m, c = e % m;
+    H[r * ld + c] = 0.5 * (hin[(size_t)c * m + r] + hin[(size_t)r * m + c]);
+    W[r * ld + c] = win[(size_t)c * m + r];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < m; i += 32) v = fmax(v, fabs(H[i * ld + i]));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) s_floor = ldexp(v, -44);
+  }
+  __syncthreads();
+  const double fl = s_floor;
+  auto needs = [&](double hpp, double hqq, double hpq) {
+    return fabs(hpq) > fl && hpq * hpq > 1e-30 * fabs(hpp * hqq) && fabs(hpq) > 1e-300;
+  };
+  int round = 0;
+  bool done = false;
+  for (; round < kSparseRounds * m; ++round) {
+    // (1) each row's best partner (one warp per row)
+    for (int p = warp; p < m; p += nwarps) {
+      double bv = 0.0;
+      int bq = -1;
+      const double hpp = H[p * ld + p];
+      for (int q = lane; q < m; q += 32) {
+        // the symmetric value: rows p and q must agree on it for the pair to be mutual
+        const double h = 0.5 * (H[p * ld + q] + H[q * ld + p]);
+        if (q != p && needs(hpp, H[q * ld + q], h) && fabs(h) > bv) {
+          bv = fabs(h);
+          bq = q;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (ov > bv || (ov == bv && oq > bq)) {
+          bv = ov;
+          bq = oq;
+        }
+      }
+      if (lane == 0) best[p] = bq;
+    }
+    if (threadIdx.x == 0) nsel = 0;
+    __syncthreads();
+    // (2) mutually best pairs, their angles
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+      const int q = best[p];
+      if (q > p && best[q] == p) {
+        const int k = atomicAdd(&nsel, 1);
+        double c, sv;
+        jacobi_angle(H[p * ld + p], H[q * ld + q], 0.5 * (H[p * ld + q] + H[q * ld + p]), c, sv);
+        selp[k] = p;
+        selq[k] = q;
+        sc[k] = c;
+        ss[k] = sv;
+      }
+    }
+    __syncthreads();
+    const int ns = nsel;
+    if (ns == 0) {
+      done = true;
+      break;
+    }
+    // (3) right factor: columns p, q of H and W
+    for (int e = threadIdx.x; e < ns * m; e += blockDim.x) {
+      const int k = e / m, r = e % m, p = selp[k], q = selq[k];
+      const double c = sc[k], sv = ss[k];
+      const double x = H[r * ld + p], y = H[r * ld + q];
+      H[r * ld + p] = c * x - sv * y;
+      H[r * ld + q] = sv * x + c * y;
+      const double wx = W[r * ld + p], wy = W[r * ld + q];
+      W[r * ld + p] = c * wx - sv * wy;
+      W[r * ld + q] = sv * wx + c * wy;
+    }
+    __syncthreads();
+    // (4) left factor: rows p, q; the rotated pair's own entries are zero
+    for (int e = threadIdx.x; e < ns * m; e += blockDim.x) {
+      const int k = e / m, col = e % m, p = selp[k], q = selq[k];
+      const double c = sc[k], sv = ss[k];
+      const double x = H[p * ld + col], y = H[q * ld + col];
+      H[p * ld + col] = (col == q) ? 0.0 : c * x - sv * y;
+      H[q * ld + col] = (col == p) ? 0.0 : sv * x + c * y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (!done) atomicExch(flag, 2);
+    atomicMax(rounds_out, round);
+  }
+  // sort descending (rank of each diagonal entry, ties by index)
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double ti = H[i * ld + i];
+    int rk = 0;
+    for (int j = 0; j < m; ++j) {
+      const double tj = H[j * ld + j];
+      rk += (tj > ti) || (tj == ti && j < i);
+    }
+    theta.at(z)[rk] = ti;
+    for (int row = 0; row < m; ++row) Wout.at(z)[(size_t)rk * m + row] = W[row * ld + i];
+  }
+}
+
 // flags.at(z)[2] = 1 if max |C_ij - delta_ij| > 1/4 (the Newton-Schulz
 // iteration for C^-1/2 from I is then not to be trusted), else 0.
 __global__ void k_rr_far_from_identity(PSet C, int m, PSet flags) {
@@ -1259,7 +1437,8 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_si_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
       (e = cudaFuncSetAttribute(k_si_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
       (e = cudaFuncSetAttribute(k_si_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
-      (e = cudaFuncSetAttribute(k_rr_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+      (e = cudaFuncSetAttribute(k_rr_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) ||
+      (e = cudaFuncSetAttribute(k_rr_sparse_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   done = true;
   return cudaSuccess;
@@ -1465,13 +1644,34 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     nl += 7;
     cudaError_t r;
     if ((r = cudaGetLastError())) return r;
-    // H' comes from two FP64 products: its entries carry rounding noise of
-    // about m u ||H|| (2^-46 at m = 72), so entries below 2^-44 of its largest
+    // FP64 finish: two first-order correction steps (k_rr_sfs_build above),
+    // W' = Q1 Q2, then the sparse Jacobi on what still needs rotating.  H'
+    // comes from two FP64 products: its entries carry rounding noise of about
+    // m u ||H|| (2^-46 at m = 72), so entries below 2^-44 of its largest
     // diagonal entry are left alone (their effect on a residual is below
-    // 1e-13 of the largest eigenvalue), and a sweep whose rotated entries all
-    // lay below 2^-42 of it (2.3e-13 of the largest Ritz value: already within
-    // the residual bound) ends the iteration
-    if ((r = launch_jacobi(V2, m, T1, B.th, B.flag, B.sweeps, P, s, 44, 42))) return r;   // T1 = W'
+    // 1e-13 of the largest eigenvalue).
+    const PSet Am = slot(4), Q0 = slot(5), Tq = slot(6), Qm = slot(7), Tt = slot(8);
+    const dim3 g1(grid_1d(L.mm, P), 1, P);
+    for (int step = 0; step < 2; ++step) {
+      k_rr_sfs_build<<<g1, 256, 0, s>>>(V2, m, Am);
+      k_rr_mm<<<gmm, 256, 0, s>>>(Am, 0, Am, 0.5, 1.0, Q0, m);       // A + A^2 / 2
+      k_rr_axpi<<<g1, 256, 0, s>>>(Q0, 1.0, 1.0, Q0, m);              // + I
+      k_rr_mm<<<gmm, 256, 0, s>>>(Q0, 1, Q0, 1.0, 0.0, Tq, m);        // Q0^T Q0
+      k_rr_mm<<<gmm, 256, 0, s>>>(Q0, 0, Tq, -0.5, 1.5, Qm, m);       // Q = Q0 (3I - Q0^T Q0) / 2
+      k_rr_mm<<<gmm, 256, 0, s>>>(V2, 0, Qm, 1.0, 0.0, Tt, m);        // H' Q
+      k_rr_mm<<<gmm, 256, 0, s>>>(Qm, 1, Tt, 1.0, 0.0, V2, m);        // H' <- Q^T H' Q
+      if (step == 0) {
+        k_si_copy<<<g1, 256, 0, s>>>(Qm, T1, L.mm);                    // W' = Q1
+        nl += 8;
+      } else {
+        k_rr_mm<<<gmm, 256, 0, s>>>(T1, 0, Qm, 1.0, 0.0, Tt, m);      // W' Q2
+        k_si_copy<<<g1, 256, 0, s>>>(Tt, T1, L.mm);
+        nl += 9;
+      }
+    }
+    k_rr_sparse_jacobi<<<gz, kSparseThreads, sparse_smem(m), s>>>(V2, m, T1, T1, B.th, B.flag, B.sweeps);
+    nl += 1;
+    if ((r = cudaGetLastError())) return r;
     k_rr_mm<<<gmm, 256, 0, s>>>(V1, 0, T1, 1.0, 0.0, B.W, m);     // W = V1 W'
     nl += 2;
     return cudaGetLastError();

@@ -688,21 +688,26 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       sb.has_trace = true;
       sb.shift_rel = 0x1.0p-40;
       // Environments built from reduced-precision products are accurate to
-      // about the operands' unit roundoff u (TF32 2^-11, two-term BF16 ~2^-17,
-      // three-term ~2^-24): eigenvalues below that level relative to the
-      // largest are noise, with eigenvectors undetermined beyond it, so a
-      // residual that stalls there is accepted (2 u; FP64-grade G: 1e-10).
+      // about the operands' unit roundoff u (TF32 2^-11, two-term BF16 ~2^-17):
+      // eigenvalues below that level relative to the largest are noise, with
+      // eigenvectors undetermined beyond it, so a residual that stalls there is
+      // accepted (2 u; FP64-grade G: 1e-10).  The three-term split represents
+      // its operands to 2^-24, below the FP32 accumulation error of its
+      // products over K = Dy^2 terms (residuals measured to stall at 1.2e-7 at
+      // D = 48): its floor is 8 x 2^-24.
       switch (c->prec) {
         case HOTRG_TF32: sb.floor_tol = 2.0 * 0x1.0p-11; break;
         case HOTRG_BF16X3: sb.floor_tol = 2.0 * 0x1.0p-17; break;
-        case HOTRG_BF16X6: sb.floor_tol = 2.0 * 0x1.0p-24; break;
+        case HOTRG_BF16X6: sb.floor_tol = 8.0 * 0x1.0p-24; break;
         default: sb.floor_tol = 0.0; break;
       }
       // the solve of the last step in this direction took iters_prev
       // iterations; a Rayleigh-Ritz step costs several iterations, so the
-      // first one is scheduled just before that count
+      // first one is scheduled just before that count -- but no later than
+      // iteration 24, after which a slow solve (a flat noise tail) needs its
+      // checks to see the residual stall
       const int di = ydir ? 1 : 0;
-      sb.first_check = g.iters_prev[di] > 0 ? std::max(3, g.iters_prev[di] - 1) : 3;
+      sb.first_check = g.iters_prev[di] > 0 ? std::min(24, std::max(3, g.iters_prev[di] - 1)) : 3;
       if (g.nprev[di] == n && g.kprev[di] <= m) {
         // the last isometry of this direction starts both sides' iteration
         sb.warm = pset_pairs(g.Uprev[di], g.Uprev[di], g.sUp);
@@ -722,7 +727,7 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       snprintf(why, sizeof(why),
                "eigensolver stopped without reaching its residual bound: %d of at most %d subspace "
                "iterations, %d Rayleigh-Ritz steps, residual %.3e, breakdown %d (1 Cholesky, 2 Jacobi "
-               "sweep limit), Jacobi sweeps FP64 %d / FP32 %d",
+               "sweep limit), FP64 finishing Jacobi rounds %d, FP32 Jacobi sweeps %d",
                r.iterations, c->eig_max_iters, r.rr, eig_res, r.breakdown, r.sweeps64, r.sweeps32);
       return fail(c, HOTRG_EEIG, why);
     }
