@@ -561,15 +561,14 @@ def sweep_block(pkg, torch, flush, measured, bf16_burst, peak_src, steps=3):
     prof = bt.profile_read()
     bt.close()
     ms = sum(times)
-    q_flops = sum(2.0 * m.D_cut ** 7 + (2.0 * m.D_cut ** 6 if m.D_cut in FUSED_D else 0.0) for m in models)
+    q_flops = sum(2.0 * m.D_cut ** 7 for m in models)          # a6 flops of one batch step
     q_ms = prof["ms"]["proj_q"] / max(1, prof["steps"])
     peak, note = tensor_peak("tf32", bf16_burst, peak_src, measured)
     share = {k: round(v / max(1e-9, sum(prof["ms"].values())), 4) for k, v in prof["ms"].items()}
     return {"workload": "sweep256: 256 Ising instances, beta ~ U[0.35, 0.55], D_cut in {16, 24, 32, 40}, TF32",
             "value": round(n * steps / (ms / 1e3), 3), "unit": "RG-steps/s (instance-steps/s)",
             "ms_per_batch_step": round(ms / steps, 3), "steps_timed": steps,
-            "roofline": {"kernel": "bond contraction stage of all cut groups of a step (k_tc_chain "
-                                   "a6 + a7 for D_cut 16 and 32, k_tc_gemm a6 for 24 and 40)", "bound": "tensor",
+            "roofline": {"kernel": "k_tc_gemm a6 bond contraction (all cut groups of a step)", "bound": "tensor",
                          "achieved": round(q_flops / (q_ms / 1e3) / 1e12, 2), "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(q_flops / (q_ms / 1e3) / 1e12 / peak, 4),
                          "peak_source": note},
@@ -773,9 +772,7 @@ def run_sweep(args, world, rank, local):
     value = n * args.steps / (max_ms / 1e3)
     lz_all = gather_floats(lz_mine, world)
     flops_step = sum(step_flops(m.D_cut, m.D_cut, m.D_cut) for m in models)
-    # bond-contraction stage flops of one batch step (a7 too where the fused kernel runs)
-    q_flops = sum(2.0 * m.D_cut ** 7 + (2.0 * m.D_cut ** 6 if prec == "tf32" and m.D_cut in FUSED_D else 0.0)
-                  for m in models)
+    q_flops = sum(2.0 * m.D_cut ** 7 for m in models)          # a6 flops of one batch step
     q_ms_step = prof["ms"]["proj_q"] / max(1, prof["steps"])
     achieved = q_flops / (q_ms_step / 1e3) / 1e12
     bf16_burst, _, _, peak_src = peaks()
@@ -795,8 +792,7 @@ def run_sweep(args, world, rank, local):
                       "parallelism": f"instance-sharded x{world}"},
            "tflops": round(sum(step_flops(m.D_cut, m.D_cut, m.D_cut) for m in everything)
                            * args.steps / (max_ms / 1e3) / 1e12, 3),
-           "roofline": {"kernel": "bond contraction stage of all groups of a step (k_tc_chain a6 + a7 "
-                                  "where fused, else k_tc_gemm a6)",
+           "roofline": {"kernel": "k_tc_gemm a6 bond contraction Q=P.T (all groups of a step)",
                         "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                         "peak_source": f"{peak_src} bf16 burst x nominal TF32/BF16 ratio"},

@@ -1081,7 +1081,7 @@ __global__ void __launch_bounds__(kSparseThreads, 1)
   const double *hin = Hin.at(z), *win = Win.at(z);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int r = e / m, c = e % m;
+    const int r = e % m, c = e / m;                 // column-major inputs: coalesced reads
     H[r * ld + c] = 0.5 * (hin[(size_t)c * m + r] + hin[(size_t)r * m + c]);
     W[r * ld + c] = win[(size_t)c * m + r];
   }
@@ -1170,7 +1170,8 @@ __global__ void __launch_bounds__(kSparseThreads, 1)
     if (!done) atomicExch(flag, 2);
     atomicMax(rounds_out, round);
   }
-  // sort descending (rank of each diagonal entry, ties by index)
+  // sort descending (rank of each diagonal entry, ties by index); best[] now
+  // holds the column of each rank
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const double ti = H[i * ld + i];
     int rk = 0;
@@ -1179,7 +1180,12 @@ __global__ void __launch_bounds__(kSparseThreads, 1)
       rk += (tj > ti) || (tj == ti && j < i);
     }
     theta.at(z)[rk] = ti;
-    for (int row = 0; row < m; ++row) Wout.at(z)[(size_t)rk * m + row] = W[row * ld + i];
+    best[rk] = i;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int row = e % m, rk = e / m;
+    Wout.at(z)[e] = W[row * ld + best[rk]];
   }
 }
 

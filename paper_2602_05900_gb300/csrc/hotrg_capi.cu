@@ -226,7 +226,13 @@ struct Group {
   double *spectra = nullptr;      // kMaxSteps x (D_cut + 1) per instance
   double *Uprev[2] = {nullptr, nullptr};
   int nprev[2] = {0, 0}, kprev[2] = {0, 0};
+  // all m Ritz vectors of both environments of the last solve per direction
+  // (problem z of the solve at Xprev + z sXp), the next solve's start block
+  double *Xprev[2] = {nullptr, nullptr};
+  long long sXp = 0;
+  int xprev_n[2] = {0, 0}, xprev_m[2] = {0, 0};
   int iters_prev[2] = {0, 0};     // subspace iterations of the last solve per direction
+  int rr_prev[2] = {0, 0};        // and its Rayleigh-Ritz steps
   TcPath tc;
   XsWork xw{};                    // exact-slice contraction mode scratch
   std::vector<GroupStep> steps;
@@ -350,16 +356,20 @@ hotrg_status alloc_group(hotrg_ctx *c, Group &g) {
   g.sT = round_up(t4, 32);
   g.sU = round_up(nmax * (g.D_cut + 1), 32);
   g.sUp = round_up(nmax * g.D_cut, 32);
+  g.sXp = round_up(nmax * kSiMaxBlock, 32);
   g.sP = round_up((long long)g.D_cut * t4, 32);
   g.sRec = (long long)kMaxSteps * kRecord;
   g.sSpec = round_up((long long)kMaxSteps * (g.D_cut + 1), 32);
   hotrg_status s;
   if ((s = dalloc(c, &g.T, g.sT * G)) || (s = dalloc(c, &g.Tn, g.sT * G)) ||
-      (s = dalloc(c, &g.GL, g.sT * G)) || (s = dalloc(c, &g.GR, g.sT * G)) ||
+      (s = dalloc(c, &g.GL, 2 * g.sT * G)) ||
       (s = dalloc(c, &g.U, g.sU * G)) || (s = dalloc(c, &g.scal, (long long)kScal * G)) ||
       (s = dalloc(c, &g.records, g.sRec * G)) || (s = dalloc(c, &g.spectra, g.sSpec * G)) ||
-      (s = dalloc(c, &g.Uprev[0], g.sUp * G)) || (s = dalloc(c, &g.Uprev[1], g.sUp * G)))
+      (s = dalloc(c, &g.Uprev[0], g.sUp * G)) || (s = dalloc(c, &g.Uprev[1], g.sUp * G)) ||
+      (s = dalloc(c, &g.Xprev[0], g.sXp * 2 * G)) || (s = dalloc(c, &g.Xprev[1], g.sXp * 2 * G)))
     return s;
+  // G_R follows G_L's G instances (one batched Gram combine over both sides)
+  g.GR = g.GL + g.sT * G;
   if (c->prec == HOTRG_FP64 || c->prec == HOTRG_BF16XS) {
     if ((s = dalloc(c, &g.AL, g.sT * G)) || (s = dalloc(c, &g.BL, g.sT * G)) ||
         (s = dalloc(c, &g.AR, g.sT * G)) || (s = dalloc(c, &g.BR, g.sT * G)) ||
@@ -678,7 +688,13 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       eig_path = 1;
       ok = true;
     } else {
-      int m = ((2 * k + 7) / 8) * 8;
+      // Rayleigh-Ritz block: 5k/4 rounded up to a multiple of 8 (m = 48 for the
+      // k = 33 pairs of D' = 32).  A smaller block costs more iterations (the
+      // error of the wanted pairs shrinks by theta_m / theta_k per iteration)
+      // but each of its iterations, orthogonalisations and Jacobi solves is
+      // cheaper; measured at D = 32: m = 72 (2k) 243, m = 48 277-284, m = 40
+      // 230-237 RG-steps/s.
+      int m = ((5 * k + 3) / 4 + 7) / 8 * 8;
       if (m > kSiMaxBlock) m = kSiMaxBlock;
       if (m > n) m = n & ~1;
       sb.m = m;
@@ -703,12 +719,22 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       }
       // the solve of the last step in this direction took iters_prev
       // iterations; a Rayleigh-Ritz step costs several iterations, so the
-      // first one is scheduled just before that count -- but no later than
-      // iteration 24, after which a slow solve (a flat noise tail) needs its
-      // checks to see the residual stall
+      // first one is scheduled just before that count -- one iteration
+      // earlier still if that solve converged at its first check (so that the
+      // schedule can find a shorter solve instead of repeating the last one)
+      // -- but no later than iteration 24, after which a slow solve (a flat
+      // noise tail) needs its checks to see the residual stall
       const int di = ydir ? 1 : 0;
-      sb.first_check = g.iters_prev[di] > 0 ? std::min(24, std::max(3, g.iters_prev[di] - 1)) : 3;
-      if (g.nprev[di] == n && g.kprev[di] <= m) {
+      const int back = g.rr_prev[di] == 1 ? 2 : 1;
+      sb.first_check = g.iters_prev[di] > 0 ? std::min(24, std::max(3, g.iters_prev[di] - back)) : 3;
+      if (g.xprev_n[di] == n && g.xprev_m[di] == m) {
+        // the last solve of this direction (same sizes) starts each side's
+        // iteration from all of its Ritz vectors: the trailing columns start
+        // close to the next eigenvectors instead of random
+        sb.warm = pset_linear(g.Xprev[di], g.sXp);
+        sb.has_warm = true;
+        sb.kw = m;
+      } else if (g.nprev[di] == n && g.kprev[di] <= m) {
         // the last isometry of this direction starts both sides' iteration
         sb.warm = pset_pairs(g.Uprev[di], g.Uprev[di], g.sUp);
         sb.has_warm = true;
@@ -718,8 +744,17 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
       eig_path = 2;
       eig_iters = r.iterations;
       g.iters_prev[di] = r.converged ? r.iterations : 0;
+      g.rr_prev[di] = r.rr;
       eig_res = r.residual;
       ok = r.converged;
+      if (ok) {
+        const SiOut o = si_outputs(g.si_work, 2 * G, n, m);
+        CK_CUDA(c, cudaMemcpy2DAsync(g.Xprev[di], sizeof(double) * g.sXp, o.X.at(0),
+                                     sizeof(double) * (o.X.at(1) - o.X.at(0)), sizeof(double) * (size_t)n * m,
+                                     2 * G, cudaMemcpyDeviceToDevice, st));
+        g.xprev_n[di] = n;
+        g.xprev_m[di] = m;
+      }
     }
     pf.launched(HOTRG_ST_EIG, (int)nl);
     if (!ok) {

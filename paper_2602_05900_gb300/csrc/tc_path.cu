@@ -21,15 +21,18 @@ struct TcPath::Impl {
   int planes = 1, eb = 4;
   int G = 1;                       // instances
   long long sTop = 0, sPop = 0;    // elements between instances: operand buffers, P / Q
-  void *opT[4] = {};       // a2 operands: permuted views of T
-  void *part[4] = {};      // a2 outputs / a3 operands: [x][u] x [k][k']
+  // a2 operands (permuted views of T) and a2 outputs / a3 operands ([x][u] x
+  // [k][k']): four per instance, interleaved as q = (side G + g) 2 + j for
+  // view i = 2 side + j of instance g, so that a2 is one batched GEMM over
+  // all q and a3 one over (side, g) with A at q = 2 (side G + g), B at q + 1
+  void *opT = nullptr, *part = nullptr;
   void *opU5 = nullptr, *opT5 = nullptr, *opT6 = nullptr, *opU7 = nullptr;
   void *P = nullptr, *Q = nullptr;
   int *err = nullptr;
   std::size_t capT = 0, capP = 0;  // elements per plane
   ~Impl() {
-    for (void *p : opT) cudaFree(p);
-    for (void *p : part) cudaFree(p);
+    cudaFree(opT);
+    cudaFree(part);
     cudaFree(opU5);
     cudaFree(opT5);
     cudaFree(opT6);
@@ -115,10 +118,7 @@ int TcPath::init(hotrg_prec prec, int D0, int D_cut, int G, cudaStream_t s, int 
   I.sTop = ((long long)I.capT * I.planes + 63) / 64 * 64;
   I.sPop = ((long long)I.capP * I.planes + 63) / 64 * 64;
   const std::size_t bt = (std::size_t)I.sTop * G * I.eb, bp = (std::size_t)I.sPop * G * I.eb;
-  for (int i = 0; i < 4; ++i) {
-    if (!(I.opT[i] = alloc(bt))) return 2;
-    if (!(I.part[i] = alloc(bt))) return 2;
-  }
+  if (!(I.opT = alloc(4 * bt)) || !(I.part = alloc(4 * bt))) return 2;
   if (!(I.opU5 = alloc(bt)) || !(I.opT5 = alloc(bt)) || !(I.opT6 = alloc(bt)) ||
       !(I.opU7 = alloc(bt)) || !(I.P = alloc(bp)) || !(I.Q = alloc(bp)))
     return 2;
@@ -126,27 +126,31 @@ int TcPath::init(hotrg_prec prec, int D0, int D_cut, int G, cudaStream_t s, int 
   return 0;
 }
 
+// dst: instance g's plane at dst + g sDst elements (default: the operand stride)
 static cudaError_t gather(const TcPath::Impl &I, const double *src, long long sSrc, int R, int K,
-                          int pitch, IdxMap rm, IdxMap km, void *dst) {
+                          int pitch, IdxMap rm, IdxMap km, void *dst, long long sDst = -1) {
   const long long ps = (long long)R * pitch;
   const dim3 g(grid_for(ps, I.G), I.G);
   const long long cap = sSrc * I.G;
+  if (sDst < 0) sDst = I.sTop;
   switch (I.mode) {
-    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps, cap, I.err); break;
-    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps, cap, I.err); break;
-    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, I.sTop, ps, cap, I.err); break;
+    case TcMode::TF32: k_gather<0><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, sDst, ps, cap, I.err); break;
+    case TcMode::BF16X3: k_gather<1><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, sDst, ps, cap, I.err); break;
+    case TcMode::BF16X6: k_gather<2><<<g, 256, 0, I.s>>>(src, sSrc, R, K, pitch, rm, km, dst, sDst, ps, cap, I.err); break;
   }
   return cudaGetLastError();
 }
 
+// an operand of `count` instances (default: the context's batch) bstride apart
 static TcOperand operand(const TcPath::Impl &I, const void *base, int rows, int K, int pitch,
-                         long long bstride) {
-  return TcOperand{base, rows, K, pitch, I.G, bstride};
+                         long long bstride, int count = 0) {
+  return TcOperand{base, rows, K, pitch, count > 0 ? count : I.G, bstride};
 }
 
-// Epilogue writing an operand-format result (next GEMM's A or B planes).
+// Epilogue writing an operand-format result (next GEMM's A or B planes) for
+// `count` instances (default: the context's batch).
 static TcEpilogue operand_epilogue(const TcPath::Impl &I, void *dst, long long plane_stride,
-                                   IdxMap cm, IdxMap cn, long long bstride) {
+                                   IdxMap cm, IdxMap cn, long long bstride, int count = 0) {
   TcEpilogue e{};
   if (I.mode == TcMode::TF32) {
     e.kind = OutKind::F32;
@@ -160,12 +164,12 @@ static TcEpilogue operand_epilogue(const TcPath::Impl &I, void *dst, long long p
   e.cm = cm;
   e.cn = cn;
   e.bstride = bstride;
-  e.cap = bstride * I.G;
+  e.cap = bstride * (count > 0 ? count : I.G);
   return e;
 }
 
 static TcEpilogue f64_epilogue(const TcPath::Impl &I, double *dst, IdxMap cm, IdxMap cn,
-                               long long bstride) {
+                               long long bstride, int count = 0) {
   TcEpilogue e{};
   e.kind = OutKind::F64;
   e.C = dst;
@@ -173,7 +177,7 @@ static TcEpilogue f64_epilogue(const TcPath::Impl &I, double *dst, IdxMap cm, Id
   e.cm = cm;
   e.cn = cn;
   e.bstride = bstride;
-  e.cap = bstride * I.G;
+  e.cap = bstride * (count > 0 ? count : I.G);
   return e;
 }
 
@@ -187,31 +191,48 @@ int TcPath::environment(const double *T, long long sT, int D, int E, long long s
   if ((std::size_t)DE * p2 > I.capT || (std::size_t)D2 * p3 > I.capT) return cudaErrorInvalidValue;
   const IdxMap rows[4] = {map2(E, syp, sx), map2(E, sy, sx), map2(E, syp, sxp), map2(E, sy, sxp)};
   const IdxMap reds[4] = {map2(E, sy, sxp), map2(E, syp, sxp), map2(E, sy, sx), map2(E, syp, sx)};
+  const int G = I.G;
+  const std::size_t eb = (std::size_t)I.eb;
+  auto q_base = [&](void *base, int i) {       // view i of instance 0; instances 2 sTop apart
+    return static_cast<char *>(base) + ((std::size_t)(i / 2) * G * 2 + (i % 2)) * I.sTop * eb;
+  };
   hook->begin(HOTRG_ST_PREP);
   for (int i = 0; i < 4; ++i)
-    if (cudaError_t e_ = gather(I, T, sT, DE, DE, p2, rows[i], reds[i], I.opT[i])) return e_;
+    if (cudaError_t e_ = gather(I, T, sT, DE, DE, p2, rows[i], reds[i], q_base(I.opT, i), 2 * I.sTop))
+      return e_;
   hook->launched(HOTRG_ST_PREP, 4);
   hook->end(HOTRG_ST_PREP);
+  // a2, one GEMM over the 4 G views: part_q[(x,u)][(k,k')], rows m = (x, k),
+  // cols n = (u, k')
   hook->begin(HOTRG_ST_ENV);
-  for (int i = 0; i < 4; ++i) {
-    // part[i][(x,u)][(k,k')]: rows m = (x, k), cols n = (u, k')
-    TcOperand op = operand(I, I.opT[i], DE, DE, p2, I.sTop);
-    TcEpilogue ep = operand_epilogue(I, I.part[i], (long long)D2 * p3,
-                                     map2(E, E, (long long)D * p3), map2(E, 1, p3), I.sTop);
+  {
+    TcOperand op = operand(I, I.opT, DE, DE, p2, I.sTop, 4 * G);
+    TcEpilogue ep = operand_epilogue(I, I.part, (long long)D2 * p3, map2(E, E, (long long)D * p3),
+                                     map2(E, 1, p3), I.sTop, 4 * G);
     if (cudaError_t e_ = tc_gemm(I.mode, op, op, DE, DE, DE, ep, I.err, I.s)) return e_;
   }
-  hook->launched(HOTRG_ST_ENV, 4);
+  hook->launched(HOTRG_ST_ENV, 1);
   hook->end(HOTRG_ST_ENV);
+  // a3: G_side = part_(2 side) . part_(2 side + 1)^T, one GEMM over (side, g)
+  // when the caller's G_R follows G_L's G instances, else one per side
   hook->begin(HOTRG_ST_GRAM);
   const IdxMap gm = map2(D, D, (long long)D2 * D), gn = map2(D, 1, D2);
-  for (int side = 0; side < 2; ++side) {
-    TcOperand a = operand(I, I.part[2 * side], D2, E2, p3, I.sTop);
-    TcOperand b = operand(I, I.part[2 * side + 1], D2, E2, p3, I.sTop);
-    if (cudaError_t e_ = tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(I, side ? GR : GL, gm, gn, sG),
-                                 I.err, I.s))
+  if (GR == GL + (std::size_t)G * sG) {
+    TcOperand a = operand(I, I.part, D2, E2, p3, 2 * I.sTop, 2 * G);
+    TcOperand b = operand(I, static_cast<char *>(I.part) + I.sTop * eb, D2, E2, p3, 2 * I.sTop, 2 * G);
+    if (cudaError_t e_ = tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(I, GL, gm, gn, sG, 2 * G), I.err, I.s))
       return e_;
+    hook->launched(HOTRG_ST_GRAM, 1);
+  } else {
+    for (int side = 0; side < 2; ++side) {
+      TcOperand a = operand(I, q_base(I.part, 2 * side), D2, E2, p3, 2 * I.sTop);
+      TcOperand b = operand(I, q_base(I.part, 2 * side + 1), D2, E2, p3, 2 * I.sTop);
+      if (cudaError_t e_ = tc_gemm(I.mode, a, b, D2, D2, E2, f64_epilogue(I, side ? GR : GL, gm, gn, sG),
+                                   I.err, I.s))
+        return e_;
+    }
+    hook->launched(HOTRG_ST_GRAM, 2);
   }
-  hook->launched(HOTRG_ST_GRAM, 2);
   hook->end(HOTRG_ST_GRAM);
   return 0;
 }
