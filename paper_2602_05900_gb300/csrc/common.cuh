@@ -103,8 +103,12 @@ struct MappedGemm {
 cudaError_t gemm_f64(const MappedGemm &g, cudaStream_t s);
 
 // elementwise.cu  (all batched over `batch` instances with the given strides)
+// G = (G + G^T) / 2 and its trace for `batch` problems sG apart: trace of
+// problem z at trace_out[z sTr], or with per_side > 0 (problems
+// side * per_side + i, the two sides of per_side instances) at
+// trace_out[i sTr + side].
 cudaError_t symmetrize_trace(double *G, int n, long long sG, double *trace_out, long long sTr,
-                             int batch, cudaStream_t s);
+                             int batch, cudaStream_t s, int per_side = 0);
 cudaError_t identity_isometry(double *U, int n, long long sU, int batch, cudaStream_t s);
 // T /= max|T| per instance, logsum += ln(max) * inv_two_pow_n, ln_c_out (may be null)
 // receives ln(max); scratch holds one word per instance (stride sScratch doubles).

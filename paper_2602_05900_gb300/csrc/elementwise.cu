@@ -36,28 +36,56 @@ __device__ double block_sum(double v) {
 }
 
 // grid (x: chunks of the n x n matrix, y: instance)
-__global__ void k_symmetrize(double *G, int n, long long sG) {
+
+// G = (G + G^T) / 2 by pairs of 32 x 32 tiles (I <= J, one block each,
+// blockIdx.y = problem): both tiles are read and written row by row through
+// shared memory, so every global access is coalesced.  Each off-diagonal pair
+// (i, j) gets 0.5 (G_ij + G_ji) in both places; diagonal entries are unchanged.
+__global__ void __launch_bounds__(256) k_symmetrize_tiled(double *G, int n, long long sG) {
+  __shared__ double A[32][33], B[32][33];
   G += blockIdx.y * sG;
-  const long long total = (long long)n * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
-    if (j > i) {
-      const double a = G[(long long)i * n + j], b = G[(long long)j * n + i];
-      const double v = 0.5 * (a + b);
-      G[(long long)i * n + j] = v;
-      G[(long long)j * n + i] = v;
-    }
+  const int T = (n + 31) / 32;
+  int p = blockIdx.x, I = 0;
+  while (p >= T - I) {
+    p -= T - I;
+    ++I;
+  }
+  const int J = I + p;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = I * 32 + r, j = J * 32 + tx;
+    A[r][tx] = (i < n && j < n) ? G[(long long)i * n + j] : 0.0;
+    const int i2 = J * 32 + r, j2 = I * 32 + tx;
+    B[r][tx] = (i2 < n && j2 < n) ? G[(long long)i2 * n + j2] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = I * 32 + r, j = J * 32 + tx;
+    const double v = 0.5 * (A[r][tx] + B[tx][r]);
+    if (i < n && j < n && i != j) G[(long long)i * n + j] = v;
+    A[r][tx] = v;
+  }
+  if (I == J) return;
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = J * 32 + r, j = I * 32 + tx;
+    if (i < n && j < n) G[(long long)i * n + j] = A[tx][r];
   }
 }
 
-// one block per instance
-__global__ void k_trace_diag(const double *G, int n, long long sG, double *out, long long sOut) {
+// one block per problem z; the trace goes to out[z sOut], or with per_side > 0
+// (problems side * per_side + i) to out[i sOut + side]
+__global__ void k_trace_diag(const double *G, int n, long long sG, double *out, long long sOut,
+                             int per_side) {
   G += blockIdx.x * sG;
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += G[(long long)i * n + i];
   v = block_sum(v);
-  if (threadIdx.x == 0) out[blockIdx.x * sOut] = v;
+  if (threadIdx.x == 0) {
+    const long long o = per_side > 0 ? (long long)(blockIdx.x % per_side) * sOut + blockIdx.x / per_side
+                                     : (long long)blockIdx.x * sOut;
+    out[o] = v;
+  }
 }
 
 __global__ void k_identity(double *U, int n, long long sU) {
@@ -230,10 +258,10 @@ int grid_for(long long count, int threads, int batch) {
 }  // namespace
 
 cudaError_t symmetrize_trace(double *G, int n, long long sG, double *trace_out, long long sTr,
-                             int batch, cudaStream_t s) {
-  const long long total = (long long)n * n;
-  k_symmetrize<<<dim3(grid_for(total, 256, batch), batch), 256, 0, s>>>(G, n, sG);
-  k_trace_diag<<<batch, 1024, 0, s>>>(G, n, sG, trace_out, sTr);
+                             int batch, cudaStream_t s, int per_side) {
+  const int T = (n + 31) / 32;
+  k_symmetrize_tiled<<<dim3(T * (T + 1) / 2, batch), 256, 0, s>>>(G, n, sG);
+  k_trace_diag<<<batch, 1024, 0, s>>>(G, n, sG, trace_out, sTr, per_side);
   return cudaGetLastError();
 }
 

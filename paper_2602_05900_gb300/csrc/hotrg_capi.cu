@@ -646,9 +646,9 @@ hotrg_status step_group(hotrg_ctx *c, Group &g, hotrg_dir dir, int step) {
   }
   // the tensor-core chain closed its own Gram stage (it may run as a graph)
   if (tc) pf.begin(HOTRG_ST_GRAM);
-  CK_CUDA(c, symmetrize_trace(g.GL, n, g.sT, g.scal + 2, kScal, G, st));
-  CK_CUDA(c, symmetrize_trace(g.GR, n, g.sT, g.scal + 3, kScal, G, st));
-  pf.launched(HOTRG_ST_GRAM, 4);
+  // both sides at once (G_R follows G_L's G instances): traces to scal + 2 + side
+  CK_CUDA(c, symmetrize_trace(g.GL, n, g.sT, g.scal + 2, kScal, 2 * G, st, G));
+  pf.launched(HOTRG_ST_GRAM, 2);
   pf.end(HOTRG_ST_GRAM);
 
   // ---- a4: FP64 eigendecomposition and choice of U

@@ -79,6 +79,26 @@ __device__ __forceinline__ void store_out(const TcEpilogue &e, long long off, fl
   }
 }
 
+// Stores 4 consecutive columns (off .. off + 3) of an F32 or F64 output at once
+// (16-byte stores; tc_gemm checked the alignment when it set e.vec4).
+__device__ __forceinline__ void store_out4(const TcEpilogue &e, long long off, float v0, float v1,
+                                           float v2, float v3, long long zoff, int *err) {
+  if (!checked_ok(zoff + off, e.cap, err) || !checked_ok(zoff + off + 3, e.cap, err)) return;
+  if (e.kind == OutKind::F32) {
+    if (e.round_tf32) {
+      v0 = round_tf32(v0);
+      v1 = round_tf32(v1);
+      v2 = round_tf32(v2);
+      v3 = round_tf32(v3);
+    }
+    *reinterpret_cast<float4 *>(static_cast<float *>(e.C) + off) = make_float4(v0, v1, v2, v3);
+  } else {
+    double2 *d = reinterpret_cast<double2 *>(static_cast<double *>(e.C) + off);
+    d[0] = make_double2(v0, v1);
+    d[1] = make_double2(v2, v3);
+  }
+}
+
 template <int MODE>
 struct ModeTraits;
 template <>
@@ -295,6 +315,24 @@ __global__ void __launch_bounds__(384, 1)
             const long long co = __shfl_sync(0xffffffffu, coff, j);
             if (rv && co >= 0) store_out(e, roff + co, __uint_as_float(r[j]), zoff, err_flag);
           }
+        } else if (e.vec4 && n0 + c * 32 + 32 <= N) {
+          // column-major staging (stage[col][row], conflict-free), then lane l
+          // stores columns 4 (l mod 8) .. + 3 of row 4 it + l / 8: eight 16-byte
+          // stores per lane and chunk instead of 32 scalar ones
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stage[j * 33 + lane] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int q = lane & 7;
+          const long long cq = map_off(e.cn, n0 + c * 32 + 4 * q);
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int rr = it * 4 + (lane >> 3);
+            const long long ro = __shfl_sync(0xffffffffu, roff, rr);
+            const float v0 = stage[(4 * q) * 33 + rr], v1 = stage[(4 * q + 1) * 33 + rr];
+            const float v2 = stage[(4 * q + 2) * 33 + rr], v3 = stage[(4 * q + 3) * 33 + rr];
+            if (ro >= 0) store_out4(e, ro + cq, v0, v1, v2, v3, zoff, err_flag);
+          }
+          __syncwarp();
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
@@ -519,6 +557,16 @@ cudaError_t tc_gemm(TcMode mode, const TcOperand &A, const TcOperand &B, int M, 
   TcEpilogue e = epi;
   // store layout: keep lane = row when the rows are unit-stride, else transpose
   e.transpose = !(epi.cm.s0 == 1 && epi.cm.n0 >= 8);
+  // transposed F32 / F64 stores 4 columns at a time where every group of 4
+  // consecutive columns is contiguous and 16-byte aligned: unit column stride,
+  // all other strides and the instance stride multiples of 4 elements
+  {
+    auto m4 = [](long long v) { return (v & 3) == 0; };
+    const IdxMap &cm = epi.cm, &cn = epi.cn;
+    e.vec4 = e.transpose && (epi.kind == OutKind::F32 || epi.kind == OutKind::F64) && cn.s0 == 1 &&
+             (cn.n0 & 3) == 0 && m4(cn.s1) && m4(cn.s2) && m4(cm.s0) && m4(cm.s1) && m4(cm.s2) &&
+             m4(epi.bstride) && (reinterpret_cast<uintptr_t>(epi.C) & 15) == 0;
+  }
   switch (mode) {
     case TcMode::TF32: return dispatch_bn<0>(A, B, M, N, K, e, err_flag, s);
     case TcMode::BF16X3: return dispatch_bn<1>(A, B, M, N, K, e, err_flag, s);

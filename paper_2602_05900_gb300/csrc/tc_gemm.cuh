@@ -47,6 +47,8 @@ struct TcEpilogue {
                            // stores 32 consecutive columns of one row (unit-stride cn)
   long long cap;           // elements of C from its base, all instances and planes (0 =
                            // unknown): bounds of the checked build
+  bool vec4;               // set by tc_gemm: transposed F32 / F64 stores of 4 consecutive
+                           // columns at once (unit-stride, 4-aligned column map)
 };
 
 // Launches C(M x N) = A(M x K) . B(N x K)^T for every instance of the batch
