@@ -193,14 +193,19 @@ __global__ void k_si_colscale(PSet C, PSet ks, int m) {
   }
 }
 
-__global__ void k_si_sum_split(PSet part, PSet out, int S, long long nm) {
+// out = sum of the S K-parts; with shift, + sig[1] X as well (the iteration's
+// shift, the same fma as k_si_shift_add) and sig[0] = sig[1]
+__global__ void k_si_sum_split(PSet part, PSet out, int S, long long nm, PSet X, PSet sig, int shift) {
   const int z = blockIdx.z;
+  const double sg = shift ? sig.at(z)[1] : 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
        e += (long long)gridDim.x * blockDim.x) {
     double v = 0.0;
     for (int s = 0; s < S; ++s) v += part.at(z)[s * nm + e];
+    if (shift) v = fma(sg, X.at(z)[e], v);
     out.at(z)[e] = v;
   }
+  if (shift && blockIdx.x == 0 && threadIdx.x == 0) sig.at(z)[0] = sg;
 }
 
 // Cp[c] = A[rows of chunk c]^T B[same rows]   (m x m, row-major a*m + b)
@@ -337,9 +342,23 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
   for (int attempt = 0; attempt < 2; ++attempt) {
     const float sh = attempt == 0 ? shift : fmaxf(shift, kChol32Retry);
     __syncthreads();
-    for (int a = ty; a < m; a += 16)
-      for (int b = tx; b < m; b += 16)
-        C[a * ld + b] = (float)Cin.at(z)[(size_t)a * m + b] * (d[a] * d[b]) + (a == b ? sh : 0.0f);
+    // coalesced reads, four in flight per thread
+    for (int e0 = threadIdx.x; e0 < m * m; e0 += 4 * blockDim.x) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < m * m ? Cin.at(z)[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < m * m) {
+          const int a = e / m, b = e % m;
+          C[a * ld + b] = (float)v[u] * (d[a] * d[b]) + (a == b ? sh : 0.0f);
+        }
+      }
+    }
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     // Blocked right-looking factorisation, panels of kCholPanel columns and two
@@ -356,55 +375,55 @@ __global__ void __launch_bounds__(kCholThreads) k_si_chol32(PSet Cin, int m, flo
       float U[kCholPanel][kCholPanel];
       float uinv[kCholPanel];
       bool ok = factor;
+      if (factor) {
+        // the block's upper triangle into registers first (rows past w: identity),
+        // then the dependent chain; 1 / u_ii by rsqrtf (an FP32 factor is all
+        // the pass needs: the FP64 rotation preserves the span whatever W is)
 #pragma unroll
-      for (int i = 0; i < kCholPanel; ++i) {
-        if (i < w && ok) {
-          float dd = C[(j0 + i) * ld + j0 + i];
+        for (int i = 0; i < kCholPanel; ++i)
+#pragma unroll
+          for (int b = i; b < kCholPanel; ++b)
+            U[i][b] = (i < w && b < w) ? C[(j0 + i) * ld + j0 + b] : (i == b ? 1.0f : 0.0f);
+#pragma unroll
+        for (int i = 0; i < kCholPanel; ++i) {
+          float dd = U[i][i];
 #pragma unroll
           for (int k = 0; k < i; ++k) dd = fmaf(-U[k][i], U[k][i], dd);
-          if (!(dd > 0.0f) || !isfinite(dd)) {
-            ok = false;
-          } else {
-            const float ui = sqrtf(dd);
-            uinv[i] = 1.0f / ui;
-            U[i][i] = ui;
+          ok = ok && dd > 0.0f && isfinite(dd);
+          const float r = rsqrtf(dd);
+          uinv[i] = r;
+          U[i][i] = dd * r;
 #pragma unroll
-            for (int b = i + 1; b < kCholPanel; ++b) {
-              if (b < w) {
-                float v = C[(j0 + i) * ld + j0 + b];
+          for (int b = i + 1; b < kCholPanel; ++b) {
+            float v = U[i][b];
 #pragma unroll
-                for (int k = 0; k < i; ++k) v = fmaf(-U[k][i], U[k][b], v);
-                U[i][b] = v * uinv[i];
-              }
-            }
+            for (int k = 0; k < i; ++k) v = fmaf(-U[k][i], U[k][b], v);
+            U[i][b] = v * r;
           }
         }
       }
       if (factor && !ok && threadIdx.x == 0) bad = 1;
-      for (int e = threadIdx.x; ok && e < w * w; e += blockDim.x) {
-        const int i = e / w, b = e % w;
-        if (b >= i) {
-          float v = 0.0f;
+      if (ok && threadIdx.x == 0) {
 #pragma unroll
-          for (int ii = 0; ii < kCholPanel; ++ii)
+        for (int i = 0; i < kCholPanel; ++i)
 #pragma unroll
-            for (int bb = 0; bb < kCholPanel; ++bb)
-              if (ii == i && bb == b) v = U[ii][bb];
-          R[(j0 + i) * ld + j0 + b] = v;
-        }
+          for (int b = i; b < kCholPanel; ++b)
+            if (b < w) R[(j0 + i) * ld + j0 + b] = U[i][b];
       }
       for (int l = j0 + w + threadIdx.x; ok && l < m; l += blockDim.x) {
-        float y[kCholPanel];
+        // a panel with columns past it is a full one (w = kCholPanel)
+        float cv[kCholPanel], y[kCholPanel];
+#pragma unroll
+        for (int i = 0; i < kCholPanel; ++i) cv[i] = C[(j0 + i) * ld + l];
 #pragma unroll
         for (int i = 0; i < kCholPanel; ++i) {
-          if (i < w) {
-            float v = C[(j0 + i) * ld + l];
+          float v = cv[i];
 #pragma unroll
-            for (int k = 0; k < i; ++k) v = fmaf(-U[k][i], y[k], v);
-            y[i] = v * uinv[i];
-            R[(j0 + i) * ld + l] = y[i];
-          }
+          for (int k = 0; k < i; ++k) v = fmaf(-U[k][i], y[k], v);
+          y[i] = v * uinv[i];
         }
+#pragma unroll
+        for (int i = 0; i < kCholPanel; ++i) R[(j0 + i) * ld + l] = y[i];
       }
       __syncthreads();
       if (bad) break;
@@ -1552,7 +1571,12 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
     nl += 1;
     return cudaGetLastError();
   };
+  // dst = G src; where the K parts are summed by a separate pass, that pass
+  // also adds the shift (shifted = true)
+  bool shifted = false;
   auto product = [&](PSet src, PSet dst) -> cudaError_t {
+    shifted = false;
+    const int sh = b.has_trace ? 1 : 0;
     if (xs) {
       const XsOperand xsl = xs_slot(L.oSb, L.oSbsc, m, n);     // rows of X^T
       cudaError_t r = xs_split(src, map1(n), map1(1), xsl, s);
@@ -1563,7 +1587,8 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       } else {
         r = xs_gemm(gs, xsl, n, m, n, B.Yp.b0, map1(1), map1(n), L.per, xsplit, L.nm, b.err, s);
         if (r) return r;
-        k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, xsplit, L.nm);
+        k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, xsplit, L.nm, src, B.sig, sh);
+        shifted = true;
         nl += 3;
       }
       return r ? r : cudaGetLastError();
@@ -1573,14 +1598,15 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
       nl += 1;
     } else {
       k_si_gemm<<<dim3((n + 63) / 64, L.S, P), 256, 0, s>>>(b.G, src, B.Yp, n, m, chunk);
-      k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, L.S, L.nm);
+      k_si_sum_split<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(B.Yp, dst, L.S, L.nm, src, B.sig, sh);
+      shifted = true;
       nl += 2;
     }
     return cudaGetLastError();
   };
   auto gemm = [&](PSet src, PSet dst) -> cudaError_t {
     cudaError_t r0 = product(src, dst);
-    return r0 ? r0 : add_shift(src, dst);
+    return r0 ? r0 : (shifted ? cudaSuccess : add_shift(src, dst));
   };
   // dst = src W (n x m times m x m, W column-major; tri: W upper triangular).
   // A CholeskyQR basis change (tri) normalises columns whose lengths can differ
@@ -1749,9 +1775,13 @@ cudaError_t si_solve(const SiBatch &b, double *work, double tol, int max_iter, c
   }
   k_si_init<<<dim3(grid_1d(L.nm, P), 1, P), 256, 0, s>>>(X, b.warm, b.has_warm ? 1 : 0, b.kw, n, m);
   nl += 1;
-  // a random start is well conditioned
-  if ((e = cholqr32(X, Z, 0.0f)) || (e = cholqr32(Z, Y, 0.0f))) return e;
-  std::swap(X, Y);
+  // a random or partly warm start is orthogonalised (well conditioned); a start
+  // from all m Ritz vectors of the previous solve is orthonormal to FP64 accuracy
+  // already (the final rotation of a Rayleigh-Ritz step)
+  if (!(b.has_warm && b.kw >= m)) {
+    if ((e = cholqr32(X, Z, 0.0f)) || (e = cholqr32(Z, Y, 0.0f))) return e;
+    std::swap(X, Y);
+  }
 
   res->converged = false;
   res->breakdown = 0;
