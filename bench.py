@@ -339,7 +339,17 @@ def eig_block(prof, steps, D, measured, info):
     fp64 = measured.get("fp64_tflops") or 1.0
     sub = [i for i in info if i.eig_path == 2]
     mean = lambda xs: round(statistics.mean(xs), 2) if xs else None
-    return {"ms_per_step": round(ms, 4), "share_of_step": None,
+    # FP64-grade products G X of both environments (the solver's largest
+    # arithmetic): 2 n^2 m flops per environment and product, block m = 5k/4
+    # rounded up to 8 (k = D + 1 wanted pairs)
+    k = D + 1
+    m = min(96, ((5 * k + 3) // 4 + 7) // 8 * 8)
+    products = statistics.mean([i.eig_iters for i in sub]) if sub else 0.0
+    gx_flops = products * 2 * (2.0 * n * n * m)
+    out_extra = {"block_m": m, "gx_fp64_grade_flops_per_step": gx_flops,
+                 "gx_fp64_grade_tflops_over_eig_time": round(gx_flops / (ms / 1e3) / 1e12, 3) if ms > 0 else None,
+                 "dense_bound_over_eig_time": round(dense / (fp64 * 1e12) * 1e3 / ms, 3) if ms > 0 else None}
+    return {**out_extra, "ms_per_step": round(ms, 4), "share_of_step": None,
             "n": n, "pairs_per_side": D + 1,
             "subspace_iterations_per_step": mean([i.eig_iters for i in sub]),
             "rayleigh_ritz_per_step": mean([i.eig_rr for i in sub]),
