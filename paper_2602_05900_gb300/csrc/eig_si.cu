@@ -15,13 +15,17 @@
 // Ritz value can sit at zero), the FP32 CholeskyQR pass restarts with a shift
 // instead of breaking down.
 //
-// One iteration:  Y = G X  ->  X = orth(Y): shifted CholeskyQR3 in FP64 until
-// the first Rayleigh-Ritz step, two FP32 CholeskyQR passes (FP64 rotation)
-// after it.  Before each Rayleigh-Ritz step two FP64 Newton-Schulz steps make
-// X orthonormal to FP64 accuracy; the step diagonalises H = X^T G X with the
-// parallel two-sided Jacobi method and rotates X, Y onto the Ritz vectors.  The
-// iteration stops when ||G x_i - theta_i x_i|| <= tol * theta_0 for i < k; the
-// next check is scheduled from the observed Ritz-value ratio theta_m / theta_k.
+// One iteration:  Y = G X  ->  X = orth(Y): CholeskyQR with FP32 Cholesky
+// factors and FP64 rotations -- two passes while the block may be ill
+// conditioned (or shifted CholeskyQR3 in FP64 for large batches), one pass once
+// its columns are close to eigenvectors, two FP64 passes where the block holds
+// numerically null directions.  A Rayleigh-Ritz step works with C0 = X^T X:
+// W = C0^(-1/2) (Newton-Schulz on the m x m side, or a shifted FP64 Cholesky
+// where C0 is far from I), H = W^T (X^T Y) W, H diagonalised by the parallel
+// two-sided Jacobi method (FP32, then an FP64 finish), and X, Y rotated onto
+// the Ritz vectors.  The iteration stops when ||G x_i - theta_i x_i|| <= tol *
+// theta_0 for i < k (or at the accuracy floor of G); the next check is
+// scheduled from the observed Ritz-value ratio theta_m / theta_k.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -1045,8 +1049,8 @@ __global__ void __launch_bounds__(kJ32Threads, 1) k_rr_jacobi32(PSet Cin, int m,
 // cluster of near-equal diagonal entries (|d_j - d_i| <= kSfsCluster |e_ij|)
 // are left out of A and resolved afterwards by exact 2 x 2 rotations
 // (Eq. 6) of the sparse Jacobi below, which only rotates the pairs that still
-// need it.  This replaces the full sweeps of the cluster Jacobi (2 sweeps x
-// (m - 1) rounds) on the nearly diagonal H'.
+// need it -- instead of full sweeps of (m - 1) rounds over all pairs, which
+// a nearly diagonal H' mostly does not need.
 constexpr double kSfsCluster = 1e3;
 
 __global__ void k_rr_sfs_build(PSet Hp, int m, PSet Aout) {
