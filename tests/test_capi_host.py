@@ -153,3 +153,18 @@ def test_option_and_emulated_gemm_argument_validation(lib):
     assert lib.hotrg_dgemm_emu(4, 4, 8, p, 8, p, 8, p, 4, 9, None) == HOTRG_EINVAL     # digits > 8
     assert lib.hotrg_dgemm_emu(-1, 4, 8, p, 8, p, 8, p, 4, 7, None) == HOTRG_EINVAL
     assert lib.hotrg_dgemm_emu(0, 4, 8, p, 8, p, 8, p, 4, 7, None) == 0                # empty: nothing to do
+
+
+def test_binding_constants_match_the_header():
+    """Every status code and option number the binding uses is the header's."""
+    import re
+    from paper_2602_05900_gb300 import capi
+    text = open(os.path.join(ROOT, "include", "hotrg.h")).read()
+    enums = {name: int(val) for name, val in re.findall(r"\b(HOTRG_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    for name in ["HOTRG_OK", "HOTRG_EINVAL", "HOTRG_ENOMEM", "HOTRG_ECUDA", "HOTRG_EEIG",
+                 "HOTRG_ENONFINITE", "HOTRG_ETIMEOUT", "HOTRG_ESTATE", "HOTRG_EBOUNDS"]:
+        assert getattr(capi, name) == enums[name], name
+    opts = {k: v for k, v in enums.items() if k.startswith("HOTRG_OPT_")}
+    assert opts, "no options in the header"
+    for name, val in opts.items():
+        assert getattr(capi, name[len("HOTRG_"):]) == val, name
