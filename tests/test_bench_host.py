@@ -152,3 +152,21 @@ def test_sweep_shards_gather_over_two_gloo_ranks():
         assert p.exitcode == 0
     for r in range(2):
         assert sorted(int(v) for v in out[r]) == list(range(256))
+
+
+def test_eig_block_work_figures():
+    """The eigensolver block: block size 5k/4 rounded up to 8, the FP64-grade
+    G X work of both environments per step, and the dense FP64 bound."""
+    class Info:
+        def __init__(self, iters):
+            self.eig_path, self.eig_iters, self.eig_rr = 2, iters, 1
+            self.eig_sweeps32, self.eig_sweeps = 3, 0
+    D, ms = 32, 2.0
+    blk = bench.eig_block({"ms": {"eig": ms}}, 1, D, {"fp64_tflops": 1.0}, [Info(8), Info(10)])
+    n, m = D * D, 48
+    assert blk["block_m"] == m
+    assert blk["gx_fp64_grade_flops_per_step"] == 9 * 2 * (2.0 * n * n * m)
+    assert abs(blk["gx_fp64_grade_tflops_over_eig_time"] - 9 * 4.0 * n * n * m / 2e-3 / 1e12) < 1e-3
+    dense = 2 * (4.0 / 3.0) * n ** 3
+    assert abs(blk["dense_bound_over_eig_time"] - dense / 1e12 * 1e3 / ms) < 1e-3
+    assert blk["subspace_iterations_per_step"] == 9
